@@ -1,0 +1,158 @@
+/*
+ * foeed.h - C ABI of the GB300 FOEED / EED inpainting library.
+ *
+ * Method: Jumakulyyev & Schultz, "Fourth-Order Anisotropic Diffusion for
+ * Inpainting and Image Compression" (arXiv 2006.10406).
+ *
+ * Problem (Sec. 2.1, Eq. inpaintingModel): given grey values f on a set K of
+ * known pixels (the mask), evolve
+ *     du/dt = -P(u) u   on the unknown pixels,   u = f on K,
+ * with reflecting (homogeneous Neumann) image borders, to a steady state.
+ *   FOEED: P(u)u = sum_ij d_ij [D(J(u_sigma)) : H(u)]_ij   (Eq. genModel), with
+ *          the fourth-order tensor D of Eq. faod_diffTensor / foad_diffTensor_entries.
+ *   EED:   P(u)u = -div(D grad u), D = g v1 v1^T + v2 v2^T   (Eq. EEDModel, diffTensor_EED).
+ * Time integration: FSI cycles of length n (Sec. 3.3),
+ *     u^{m,k+1} = alpha_k (u^{m,k} - tau P(u^{m,k}) u^{m,k}) + (1 - alpha_k) u^{m,k-1},
+ *     alpha_k = (4k+2)/(2k+3),  u^{m,-1} = u^{m,0},  u^{m+1,0} = u^{m,n}.
+ *
+ * Conventions for every entry point:
+ *   - Images are w columns (x, fastest) by h rows (y), row-major, with a row
+ *     pitch given in ELEMENTS (pitch >= w). The uint8 mask uses the same pitch,
+ *     counted in bytes. Nonzero mask = known pixel.
+ *   - All data pointers are DEVICE pointers owned by the caller. The library
+ *     never allocates device memory: scratch comes from the caller's workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Errors are returned as foeed_status codes; nothing aborts or throws across
+ *     the ABI. foeed_last_error() gives a thread-local message for the last
+ *     failing call on the calling thread.
+ *   - dtype selects the storage and arithmetic type of the images: FOEED_F32
+ *     (stencils in float, all reductions in double) or FOEED_F64 (double throughout).
+ *     The mixed-precision FOEED_F32_F64U keeps images in float but evaluates the
+ *     FSI extrapolation update in double.
+ */
+#ifndef FOEED_H
+#define FOEED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FOEED_OK = 0,
+    FOEED_ERR_ARG = 1,           /* invalid argument (sizes, pointers, parameters, workspace too small) */
+    FOEED_ERR_CUDA = 2,          /* a CUDA runtime call failed; see foeed_last_error() */
+    FOEED_ERR_NOT_CONVERGED = 3, /* tol > 0 and max_cycles reached first; result is still written */
+    FOEED_ERR_DIVERGED = 4,      /* a cycle produced a non-finite change; result is written as is */
+    FOEED_ERR_TIMEOUT = 5        /* reserved for bounded device waits */
+} foeed_status;
+
+typedef enum { FOEED_F32 = 0, FOEED_F64 = 1, FOEED_F32_F64U = 2 } foeed_dtype;
+
+/* Diffusivity g(s^2), s = |grad u_sigma| (Eq. CharDiff; Table 6). */
+typedef enum {
+    FOEED_G_CHARBONNIER = 0,   /* 1/sqrt(1 + s^2/lambda^2) (paper default) */
+    FOEED_G_PERONA_MALIK = 1,  /* 1/(1 + s^2/lambda^2) */
+    FOEED_G_PERONA_MALIK2 = 2, /* exp(-s^2/lambda^2) */
+    FOEED_G_AUBERT = 3,        /* (s/lambda)^2/(s^2+lambda^2)^2, as printed in Table 6 */
+    FOEED_G_GEMAN_REYNOLDS = 4 /* 2 lambda^2/(s^2+lambda^2)^2, as printed in Table 6 */
+} foeed_diffusivity;
+
+/* Eigenvalue mu_3 of the mixed eigentensor E3 (Sec. 3.1, Table 1). */
+typedef enum {
+    FOEED_MU3_GEOMETRIC = 0,  /* sqrt(mu1 mu2) = sqrt(g): the paper's choice */
+    FOEED_MU3_ARITHMETIC = 1, /* (mu1 + mu2)/2 */
+    FOEED_MU3_ONE = 2         /* max(mu1, mu2) = 1 */
+} foeed_mu3_mode;
+
+typedef struct {
+    double lambda;    /* contrast parameter of g (> 0) */
+    double sigma;     /* Gaussian pre-smoothing scale (>= 0; radius ceil(3 sigma) <= 6) */
+    double tau;       /* explicit step size; <= 0 selects 0.05 (FOEED) or 0.25 (EED), Sec. 3.1 */
+    int cycle_len;    /* FSI cycle length n >= 1 */
+    int max_cycles;   /* number of cycles (tol == 0) or cycle cap (tol > 0), >= 1 */
+    double tol;       /* > 0: stop after the first cycle with |u^{m,n}-u^{m,0}|_2/|u^{m,n}|_2 < tol */
+    int diffusivity;  /* foeed_diffusivity */
+    int mu3_mode;     /* foeed_mu3_mode (FOEED only) */
+    int init_mode;    /* 0: unknown pixels start at the mean of f over K; 1: at u_inout */
+    int check_every;  /* tol > 0: cycles between host polls of the device stop flag (<= 0: 8) */
+} foeed_params;
+
+typedef struct {
+    int cycles_run;         /* cycles executed (the stop test is exact per cycle) */
+    double last_rel_change; /* |u^{m,n}-u^{m,0}|_2 / |u^{m,n}|_2 of the last cycle run */
+    int converged;          /* 1 if tol > 0 and the stop test passed */
+    float ms;               /* device time of the solve (CUDA events), milliseconds */
+} foeed_report;
+
+/* Bytes of device workspace foeed_inpaint / eed_inpaint need for a w x h image. */
+size_t foeed_workspace_bytes(int w, int h, foeed_dtype dtype);
+
+/*
+ * Full inpainting solve by FOEED (Eq. genModel) with FSI cycles (Sec. 3.3).
+ *   f        [h x pitch] known grey values, read only where mask != 0
+ *   mask     [h x pitch] uint8, nonzero = known pixel (Dirichlet data, Eq. inpaintingModel)
+ *   u_inout  [h x pitch] result; read on entry only if init_mode == 1
+ *   workspace: device buffer of at least foeed_workspace_bytes(w, h, dtype)
+ *              bytes, 256-byte aligned; contents on entry are ignored.
+ *   report   may be NULL.
+ * Stream-ordered on `stream`; returns after the result is written (the call
+ * synchronises `stream` once at the end, and every check_every cycles when tol > 0).
+ * On return the known pixels of u_inout equal f bitwise.
+ * u_inout may alias f.
+ */
+foeed_status foeed_inpaint(const void *f, const uint8_t *mask, void *u_inout, int w, int h,
+                           long pitch, foeed_dtype dtype, const foeed_params *params,
+                           void *workspace, size_t workspace_bytes, void *stream,
+                           foeed_report *report);
+
+/* Same as foeed_inpaint with second-order EED (Eq. EEDModel, Eq. diffTensor_EED).
+ * mu3_mode is ignored; tau <= 0 selects 0.25. */
+foeed_status eed_inpaint(const void *f, const uint8_t *mask, void *u_inout, int w, int h,
+                         long pitch, foeed_dtype dtype, const foeed_params *params,
+                         void *workspace, size_t workspace_bytes, void *stream,
+                         foeed_report *report);
+
+/*
+ * One masked FSI step of FOEED (Sec. 3.3, FSI equation):
+ *   unknown: u_next = alpha (u_cur - tau P(u_cur) u_cur) + (1 - alpha) u_prev
+ *   known:   u_next = u_cur (bitwise)
+ * Uses params->lambda, sigma, tau (<= 0: 0.05), diffusivity, mu3_mode.
+ * u_next may alias u_prev but not u_cur. mask may be NULL (no known pixels:
+ * the smoothing variant). Asynchronous on `stream`; no workspace.
+ */
+foeed_status foeed_step(const void *u_prev, const void *u_cur, void *u_next, const uint8_t *mask,
+                        int w, int h, long pitch, foeed_dtype dtype, double alpha,
+                        const foeed_params *params, void *stream);
+
+/* One masked FSI step of EED; same contract as foeed_step (tau <= 0: 0.25). */
+foeed_status eed_step(const void *u_prev, const void *u_cur, void *u_next, const uint8_t *mask,
+                      int w, int h, long pitch, foeed_dtype dtype, double alpha,
+                      const foeed_params *params, void *stream);
+
+/* Bytes of workspace foeed_errors needs for a w x h image. */
+size_t foeed_errors_workspace_bytes(int w, int h);
+
+/*
+ * Error metrics of Sec. 3.2 over all w*h pixels, reduced in double:
+ *   out[0] = MSE, out[1] = AAE, out[2] = PSNR in dB for a peak of 1
+ *   (10 log10(1/MSE); +inf when MSE == 0; not in the paper).
+ * u and v are device images of the given dtype (FOEED_F32_F64U reads float).
+ * Synchronises `stream`; out is a host pointer to 3 doubles.
+ */
+foeed_status foeed_errors(const void *u, const void *v, int w, int h, long pitch, foeed_dtype dtype,
+                          void *workspace, size_t workspace_bytes, void *stream, double *out);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *foeed_last_error(void);
+
+/* Library version string. */
+const char *foeed_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOEED_H */

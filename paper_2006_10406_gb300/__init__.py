@@ -1,0 +1,259 @@
+"""GB300-native FOEED / EED sparse-mask inpainting (arXiv 2006.10406).
+
+Thin Python binding over the C ABI of libfoeed_gb300.so (include/foeed.h).
+Every step of the solve runs in the library's CUDA kernels; this module only
+marshals arguments: it takes torch tensors (device memory and streams come
+from PyTorch), passes raw pointers, sizes and the stream, and turns status
+codes into exceptions. There is no CPU fallback: without the compiled library
+or without a CUDA device every call raises.
+
+Entry points (names follow the C ABI):
+  foeed_inpaint, eed_inpaint   full FSI solve (Sec. 3.3) of Eq. genModel / Eq. EEDModel
+  foeed_step, eed_step         one masked FSI step
+  foeed_errors                 MSE / AAE (Sec. 3.2) and PSNR
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_step", "eed_step", "foeed_errors", "workspace_bytes",
+           "Report", "FoeedError", "lib", "F32", "F64", "F32_F64U", "STATUS"]
+
+F32, F64, F32_F64U = 0, 1, 2
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_CONVERGED", 4: "ERR_DIVERGED", 5: "ERR_TIMEOUT"}
+DIFFUSIVITY = {"charbonnier": 0, "perona_malik": 1, "perona_malik2": 2, "aubert": 3, "geman_reynolds": 4}
+MU3 = {"geometric": 0, "arithmetic": 1, "one": 2}
+
+
+class FoeedError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("sigma", C.c_double), ("tau", C.c_double),
+                ("cycle_len", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double),
+                ("diffusivity", C.c_int), ("mu3_mode", C.c_int), ("init_mode", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class _Report(C.Structure):
+    _fields_ = [("cycles_run", C.c_int), ("last_rel_change", C.c_double), ("converged", C.c_int),
+                ("ms", C.c_float)]
+
+
+@dataclass
+class Report:
+    status: int
+    cycles_run: int
+    last_rel_change: float
+    converged: bool
+    ms: float
+
+
+_lib = None
+
+
+def lib():
+    """Load libfoeed_gb300.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        L.foeed_workspace_bytes.argtypes = [i, i, i]
+        L.foeed_workspace_bytes.restype = sz
+        for name in ("foeed_inpaint", "eed_inpaint"):
+            fn = getattr(L, name)
+            fn.argtypes = [vp, vp, vp, i, i, C.c_long, i, C.POINTER(_Params), vp, sz, vp, C.POINTER(_Report)]
+            fn.restype = i
+        for name in ("foeed_step", "eed_step"):
+            fn = getattr(L, name)
+            fn.argtypes = [vp, vp, vp, vp, i, i, C.c_long, i, d, C.POINTER(_Params), vp]
+            fn.restype = i
+        L.foeed_errors_workspace_bytes.argtypes = [i, i]
+        L.foeed_errors_workspace_bytes.restype = sz
+        L.foeed_errors.argtypes = [vp, vp, i, i, C.c_long, i, vp, sz, vp, C.POINTER(C.c_double)]
+        L.foeed_errors.restype = i
+        L.foeed_last_error.restype = C.c_char_p
+        L.foeed_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise FoeedError(2, "no CUDA device: the FOEED library runs on the GPU only")
+    return torch
+
+
+def _check(status):
+    if status != 0:
+        raise FoeedError(status, lib().foeed_last_error().decode())
+
+
+def _dtype_code(t, dtype):
+    if dtype is not None:
+        return {"f32": F32, "f64": F64, "f32_f64u": F32_F64U, F32: F32, F64: F64, F32_F64U: F32_F64U}[dtype]
+    import torch
+    return F64 if t.dtype == torch.float64 else F32
+
+
+def _params(lam, sigma, tau=0.0, cycle_len=1, max_cycles=1, tol=0.0, diffusivity=0, mu3_mode=0,
+            init_mode=0, check_every=8):
+    if isinstance(diffusivity, str):
+        diffusivity = DIFFUSIVITY[diffusivity]
+    if isinstance(mu3_mode, str):
+        mu3_mode = MU3[mu3_mode]
+    return _Params(float(lam), float(sigma), float(tau), int(cycle_len), int(max_cycles), float(tol),
+                   int(diffusivity), int(mu3_mode), int(init_mode), int(check_every))
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _as_device_image(a, dtype, device):
+    """2-D device tensor with unit column stride (row pitch = stride(0))."""
+    torch = _torch()
+    t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+    if t.dim() != 2:
+        raise FoeedError(1, "images must be 2-D [h, w]")
+    if t.dtype != dtype:
+        t = t.to(dtype)
+    if t.device.type != "cuda":
+        t = t.pin_memory().to(device, non_blocking=True) if t.numel() else t.to(device)
+    if t.stride(1) != 1:
+        t = t.contiguous()
+    return t
+
+
+def workspace_bytes(w, h, dtype=F32):
+    """Device workspace bytes the inpaint solvers need for a w x h image."""
+    return int(lib().foeed_workspace_bytes(int(w), int(h), int(dtype)))
+
+
+def _inpaint(method, f, mask, lam, sigma, cycle_len, max_cycles, tau=0.0, tol=0.0, diffusivity=0, mu3_mode=0,
+             init_mode=0, u0=None, dtype=None, check_every=8, stream=None, workspace=None, raise_on_status=True,
+             device=None):
+    torch = _torch()
+    dev = torch.device(device) if device is not None else (
+        f.device if isinstance(f, torch.Tensor) and f.is_cuda else torch.device("cuda", torch.cuda.current_device()))
+    host_out = not (isinstance(f, torch.Tensor) and f.is_cuda)
+    if dtype is not None:
+        code = _dtype_code(None, dtype)
+    elif isinstance(f, torch.Tensor):
+        code = F64 if f.dtype == torch.float64 else F32
+    else:
+        code = F64 if np.asarray(f).dtype == np.float64 else F32
+    tdt = torch.float64 if code == F64 else torch.float32
+    fd = _as_device_image(f, tdt, dev)
+    h, w = fd.shape
+    pitch = fd.stride(0)
+    md = _as_device_image(mask, torch.uint8, dev)
+    if md.shape != fd.shape:
+        raise FoeedError(1, "mask shape differs from image shape")
+    if md.stride(0) != pitch:
+        md = _pitched_like(md, pitch)
+    u = torch.empty_strided((h, w), (pitch, 1), dtype=tdt, device=dev)
+    if u0 is not None:
+        u.copy_(_as_device_image(u0, tdt, dev))
+        init_mode = 1
+    nbytes = workspace_bytes(w, h, code)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    p = _params(lam, sigma, tau, cycle_len, max_cycles, tol, diffusivity, mu3_mode, init_mode, check_every)
+    rep = _Report()
+    fn = lib().foeed_inpaint if method == 0 else lib().eed_inpaint
+    with torch.cuda.device(dev):
+        st = fn(C.c_void_p(fd.data_ptr()), C.c_void_p(md.data_ptr()), C.c_void_p(u.data_ptr()), w, h, pitch, code,
+                C.byref(p), C.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream), C.byref(rep))
+    if st not in (0, 3, 4) or (raise_on_status and st != 0):
+        _check(st)
+    report = Report(st, rep.cycles_run, rep.last_rel_change, bool(rep.converged), rep.ms)
+    if host_out:
+        u = u.cpu()
+    return u, report
+
+
+def _pitched_like(t, pitch):
+    torch = _torch()
+    out = torch.empty_strided(t.shape, (pitch, 1), dtype=t.dtype, device=t.device)
+    out.copy_(t)
+    return out
+
+
+def foeed_inpaint(f, mask, lam, sigma, cycle_len, max_cycles, **kw):
+    """FOEED inpainting solve (Eq. genModel, FSI of Sec. 3.3). Returns (u, Report).
+
+    f, mask: [h, w] tensors or arrays (device tensors stay on the device; host
+    inputs are copied in and the result copied back). Keyword arguments:
+    tau (<= 0: 0.05), tol (0: run exactly max_cycles), diffusivity, mu3_mode,
+    init_mode, u0, dtype ('f32' | 'f64' | 'f32_f64u'), check_every, stream,
+    workspace, raise_on_status."""
+    return _inpaint(0, f, mask, lam, sigma, cycle_len, max_cycles, **kw)
+
+
+def eed_inpaint(f, mask, lam, sigma, cycle_len, max_cycles, **kw):
+    """Second-order EED solve (Eq. EEDModel), same arguments as foeed_inpaint (tau <= 0: 0.25)."""
+    return _inpaint(1, f, mask, lam, sigma, cycle_len, max_cycles, **kw)
+
+
+def _step(method, u_prev, u_cur, u_next, mask, alpha, lam, sigma, tau=0.0, diffusivity=0, mu3_mode=0,
+          dtype=None, stream=None):
+    torch = _torch()
+    for t in (u_prev, u_cur, u_next):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2 and t.stride(1) == 1):
+            raise FoeedError(1, "step images must be 2-D CUDA tensors with unit column stride")
+    h, w = u_cur.shape
+    pitch = u_cur.stride(0)
+    if u_prev.stride(0) != pitch or u_next.stride(0) != pitch:
+        raise FoeedError(1, "all step images must share one row pitch")
+    code = _dtype_code(u_cur, dtype)
+    mptr = None
+    if mask is not None:
+        if mask.dtype != torch.uint8 or mask.stride(0) != pitch or not mask.is_cuda:
+            raise FoeedError(1, "mask must be a CUDA uint8 tensor with the images' row pitch")
+        mptr = C.c_void_p(mask.data_ptr())
+    p = _params(lam, sigma, tau, diffusivity=diffusivity, mu3_mode=mu3_mode)
+    fn = lib().foeed_step if method == 0 else lib().eed_step
+    with torch.cuda.device(u_cur.device):
+        _check(fn(C.c_void_p(u_prev.data_ptr()), C.c_void_p(u_cur.data_ptr()), C.c_void_p(u_next.data_ptr()), mptr,
+                  w, h, pitch, code, float(alpha), C.byref(p), _stream_ptr(stream)))
+    return u_next
+
+
+def foeed_step(u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw):
+    """One masked FOEED FSI step into u_next (device tensors, shared pitch)."""
+    return _step(0, u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw)
+
+
+def eed_step(u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw):
+    """One masked EED FSI step into u_next."""
+    return _step(1, u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw)
+
+
+def foeed_errors(u, v, dtype=None, stream=None):
+    """(MSE, AAE, PSNR) of two device images over all pixels (Sec. 3.2), reduced in double."""
+    torch = _torch()
+    if u.shape != v.shape or u.stride(0) != v.stride(0) or u.stride(1) != 1 or v.stride(1) != 1:
+        raise FoeedError(1, "u and v must have the same shape and row pitch")
+    h, w = u.shape
+    code = _dtype_code(u, dtype)
+    nbytes = int(lib().foeed_errors_workspace_bytes(w, h))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=u.device)
+    out = (C.c_double * 3)()
+    with torch.cuda.device(u.device):
+        _check(lib().foeed_errors(C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr()), w, h, u.stride(0), code,
+                                  C.c_void_p(ws.data_ptr()), nbytes, _stream_ptr(stream), out))
+    return float(out[0]), float(out[1]), float(out[2])

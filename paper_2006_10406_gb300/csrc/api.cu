@@ -1,0 +1,543 @@
+// C ABI of the FOEED / EED inpainting library (declared in include/foeed.h).
+//
+// Host side of the solver: argument checks, workspace layout, the
+// initialisation / copy / metric kernels, and the FSI cycle driver. One FSI
+// cycle (n fused step kernels, the last one with the cycle residual) is
+// captured once into a CUDA graph and replayed; a device stop flag makes
+// every later kernel return at once after convergence, so the host only polls
+// every few cycles.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "dispatch.h"
+#include "foeed.h"
+
+using namespace foeed;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+foeed_status fail(foeed_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(FOEED_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_size(foeed_dtype d) { return d == FOEED_F64 ? 8 : 4; }
+
+// Internal row pitch (elements): rows start on 128-byte boundaries.
+long internal_pitch(int w, foeed_dtype d) { return (long)align_up((size_t)w, d == FOEED_F64 ? 16 : 32); }
+
+int tile_w(foeed_dtype d) { return d == FOEED_F64 ? kTileW64 : kTileW32; }
+int tile_h(foeed_dtype d) { return d == FOEED_F64 ? kTileH64 : kTileH32; }
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocksMax = 1024;
+
+long long max_blocks(int w, int h, foeed_dtype d)
+{
+    long long step = (long long)((w + tile_w(d) - 1) / tile_w(d)) * ((h + tile_h(d) - 1) / tile_h(d));
+    return step > kRedBlocksMax ? step : kRedBlocksMax;
+}
+
+struct Layout {
+    size_t ctl, partials, bufC, bufA, bufB, mask, total;
+    long P;
+};
+
+Layout layout(int w, int h, foeed_dtype d)
+{
+    Layout L;
+    L.P = internal_pitch(w, d);
+    size_t img = align_up((size_t)h * L.P * elem_size(d), kAlign);
+    size_t off = 0;
+    L.ctl = off; off += align_up(sizeof(Ctl), kAlign);
+    L.partials = off; off += align_up(sizeof(double) * 2 * (size_t)max_blocks(w, h, d), kAlign);
+    L.bufC = off; off += img;
+    L.bufA = off; off += img;
+    L.bufB = off; off += img;
+    L.mask = off; off += align_up((size_t)h * L.P, kAlign);
+    L.total = off;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up, copy and metric kernels (grid-stride over pixels).
+
+// Internal mask copy (0/1) and the sums of f over the known set.
+template <typename T>
+__global__ void prep_kernel(const T *__restrict__ f, const uint8_t *__restrict__ mask, uint8_t *__restrict__ mi,
+                            int w, int h, long pitch, long P, Ctl *ctl, double *partials)
+{
+    __shared__ double red[64];
+    double s = 0.0, cnt = 0.0;
+    const long n = (long)w * h;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        uint8_t k = mask[y * pitch + x] != 0;
+        mi[y * P + x] = k;
+        if (k) { s += double(f[y * pitch + x]); cnt += 1.0; }
+    }
+    if (grid_sum2_last(s, cnt, partials, &ctl->ticket, gridDim.x, blockIdx.x, red)) {
+        ctl->known = (long long)cnt;
+        ctl->mean = cnt > 0.0 ? s / cnt : 0.0;
+    }
+}
+
+// u^{0,0}: known pixels take f, unknown pixels the mean (mode 0) or u_inout (mode 1).
+template <typename T>
+__global__ void init_kernel(const T *__restrict__ f, const uint8_t *__restrict__ mi, const T *__restrict__ uin,
+                            T *__restrict__ C, int w, int h, long pitch, long P, int init_mode, const Ctl *ctl)
+{
+    const long n = (long)w * h;
+    const T mean = T(ctl->mean);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        T v;
+        if (mi[y * P + x]) v = f[y * pitch + x];
+        else v = init_mode == 0 ? mean : uin[y * pitch + x];
+        C[y * P + x] = v;
+    }
+}
+
+template <typename T>
+__global__ void copy_out_kernel(const T *__restrict__ src, T *__restrict__ dst, int w, int h, long P, long pitch)
+{
+    const long n = (long)w * h;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        dst[y * pitch + x] = src[y * P + x];
+    }
+}
+
+template <typename T>
+__global__ void errors_kernel(const T *__restrict__ u, const T *__restrict__ v, int w, int h, long pitch,
+                              Ctl *ctl, double *partials)
+{
+    __shared__ double red[64];
+    double se = 0.0, ae = 0.0;
+    const long n = (long)w * h;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        double d = double(u[y * pitch + x]) - double(v[y * pitch + x]);
+        se += d * d;
+        ae += fabs(d);
+    }
+    if (grid_sum2_last(se, ae, partials, &ctl->ticket, gridDim.x, blockIdx.x, red)) {
+        double mse = se / double(n), aae = ae / double(n);
+        ctl->err[0] = mse;
+        ctl->err[1] = aae;
+        ctl->err[2] = mse > 0.0 ? 10.0 * log10(1.0 / mse) : INFINITY;
+    }
+}
+
+int grid_for(long n)
+{
+    long b = (n + kRedThreads - 1) / kRedThreads;
+    if (b < 1) b = 1;
+    return (int)(b > kRedBlocksMax ? kRedBlocksMax : b);
+}
+
+// ---------------------------------------------------------------------------
+// Parameter checks and the step launch shared by every entry point.
+
+int gauss_radius(double sigma) { return sigma > 0.0 ? (int)std::ceil(3.0 * sigma) : 0; }
+
+// Sampled, truncated, normalised Gaussian taps (pre-smoothing of Sec. 2.2).
+template <typename T>
+void gauss_taps(double sigma, T *out)
+{
+    int R = gauss_radius(sigma);
+    double wv[2 * kRMax + 1], sum = 0.0;
+    for (int t = -R; t <= R; ++t) {
+        double v = sigma > 0.0 ? std::exp(-double(t) * t / (2.0 * sigma * sigma)) : 1.0;
+        wv[t + R] = v;
+        sum += v;
+    }
+    for (int t = 0; t <= 2 * R; ++t) out[t] = T(wv[t] / sum);
+    for (int t = 2 * R + 1; t < 2 * kRMax + 1; ++t) out[t] = T(0);
+}
+
+foeed_status check_params(const foeed_params *p, bool need_cycles)
+{
+    if (!p) return fail(FOEED_ERR_ARG, "params is NULL");
+    if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return fail(FOEED_ERR_ARG, "lambda must be > 0");
+    if (!(p->sigma >= 0.0) || gauss_radius(p->sigma) > kRMax)
+        return fail(FOEED_ERR_ARG, "sigma must be in [0, 2] (Gaussian radius ceil(3 sigma) <= %d)", kRMax);
+    if (!std::isfinite(p->tau)) return fail(FOEED_ERR_ARG, "tau must be finite");
+    if (p->diffusivity < 0 || p->diffusivity > 4) return fail(FOEED_ERR_ARG, "unknown diffusivity %d", p->diffusivity);
+    if (p->mu3_mode < 0 || p->mu3_mode > 2) return fail(FOEED_ERR_ARG, "unknown mu3_mode %d", p->mu3_mode);
+    if (need_cycles) {
+        if (p->cycle_len < 1) return fail(FOEED_ERR_ARG, "cycle_len must be >= 1");
+        if (p->max_cycles < 1) return fail(FOEED_ERR_ARG, "max_cycles must be >= 1");
+        if (!(p->tol >= 0.0)) return fail(FOEED_ERR_ARG, "tol must be >= 0");
+        if (p->init_mode != 0 && p->init_mode != 1) return fail(FOEED_ERR_ARG, "init_mode must be 0 or 1");
+    }
+    return FOEED_OK;
+}
+
+foeed_status check_image(int w, int h, long pitch, foeed_dtype d)
+{
+    if (w < 1 || h < 1) return fail(FOEED_ERR_ARG, "image size %d x %d must be >= 1 x 1", w, h);
+    if ((long long)w * h > (1LL << 31) - 1) return fail(FOEED_ERR_ARG, "image too large");
+    if (pitch < w) return fail(FOEED_ERR_ARG, "pitch %ld < width %d", pitch, w);
+    if (d != FOEED_F32 && d != FOEED_F64 && d != FOEED_F32_F64U) return fail(FOEED_ERR_ARG, "unknown dtype %d", (int)d);
+    return FOEED_OK;
+}
+
+double default_tau(bool eed, double tau) { return tau > 0.0 ? tau : (eed ? 0.25 : 0.05); }
+
+struct StepCall {
+    const void *uprev, *ucur, *c0;
+    void *unext;
+    const uint8_t *mask;
+    int w, h;
+    long pitch;
+    double alpha, tau;
+    Ctl *ctl;
+    double *partials;
+    int residual, check_done;
+};
+
+template <typename T>
+StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
+{
+    StepArgs<T> a;
+    a.uprev = static_cast<const T *>(c.uprev);
+    a.ucur = static_cast<const T *>(c.ucur);
+    a.unext = static_cast<T *>(c.unext);
+    a.mask = c.mask;
+    a.c0 = static_cast<const T *>(c.c0);
+    a.w = c.w;
+    a.h = c.h;
+    a.pitch = c.pitch;
+    a.alpha = c.alpha;
+    a.tau = c.tau;
+    a.lambda = p.lambda;
+    a.g_kind = p.diffusivity;
+    a.mu3_mode = p.mu3_mode;
+    gauss_taps<T>(p.sigma, a.wts);
+    a.ctl = c.ctl;
+    a.partials = c.partials;
+    a.residual = c.residual;
+    a.check_done = c.check_done;
+    return a;
+}
+
+// c == nullptr: only prepare the kernel (shared-memory attribute), no launch.
+cudaError_t launch_step(bool eed, foeed_dtype d, const StepCall *c, const foeed_params &p, cudaStream_t s)
+{
+    int R = gauss_radius(p.sigma);
+    if (d == FOEED_F64) {
+        StepArgs<double> a;
+        if (c) a = make_args<double>(*c, p);
+        return eed ? step_eed_f64(c ? &a : nullptr, R, s) : step_foeed_f64(c ? &a : nullptr, R, s);
+    }
+    StepArgs<float> a;
+    if (c) a = make_args<float>(*c, p);
+    bool f64u = d == FOEED_F32_F64U;
+    return eed ? step_eed_f32(c ? &a : nullptr, R, f64u, s) : step_foeed_f32(c ? &a : nullptr, R, f64u, s);
+}
+
+// ---------------------------------------------------------------------------
+// Cycle graphs: one captured FSI cycle per (method, sizes, params, buffers).
+
+struct GraphKey {
+    int eed, dtype, w, h, n, g, mu3, dev;
+    double lambda, sigma, tau;
+    const void *base;
+    long pitch;
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long stamp = 0;
+};
+
+constexpr int kCache = 4;
+GraphEntry g_cache[kCache];
+unsigned long long g_clock = 0;
+std::mutex g_mu;
+cudaStream_t g_capture_stream[64] = {};
+
+foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L,
+                           char *ws, int dev, cudaGraphExec_t *out)
+{
+    cudaStream_t cs = g_capture_stream[dev & 63];
+    if (!cs) {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        g_capture_stream[dev & 63] = cs;
+    }
+    void *C = ws + L.bufC, *A = ws + L.bufA, *B = ws + L.bufB;
+    void *buf[2] = {A, B};
+    const uint8_t *mi = reinterpret_cast<const uint8_t *>(ws + L.mask);
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    double *partials = reinterpret_cast<double *>(ws + L.partials);
+    const int n = p.cycle_len;
+    const double tau = default_tau(eed, p.tau);
+    const size_t img_bytes = (size_t)h * L.P * elem_size(d);
+
+    CK(launch_step(eed, d, nullptr, p, cs));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < n && err == cudaSuccess; ++k) {
+        StepCall c{};
+        c.w = w; c.h = h; c.pitch = L.P; c.mask = mi;
+        c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
+        c.tau = tau;
+        c.ctl = ctl; c.partials = partials; c.check_done = 1;
+        const bool last = (k == n - 1);
+        if (k == 0) { c.uprev = C; c.ucur = C; c.unext = A; }
+        else if (k == 1) { c.uprev = C; c.ucur = A; c.unext = last ? C : B; }
+        else { c.uprev = buf[k % 2]; c.ucur = buf[(k + 1) % 2]; c.unext = last ? C : buf[k % 2]; }
+        if (last) { c.residual = 1; c.c0 = C; }
+        err = launch_step(eed, d, &c, p, cs);
+        if (err == cudaSuccess && last && n == 1) err = cudaMemcpyAsync(C, A, img_bytes, cudaMemcpyDeviceToDevice, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(FOEED_ERR_CUDA, "capturing the FSI cycle: %s", cudaGetErrorString(err));
+    }
+    if (e2 != cudaSuccess) return fail(FOEED_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) return fail(FOEED_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+    return FOEED_OK;
+}
+
+foeed_status get_cycle_graph(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L,
+                             char *ws, cudaGraphExec_t *out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.eed = eed; key.dtype = d; key.w = w; key.h = h; key.n = p.cycle_len;
+    key.g = p.diffusivity; key.mu3 = eed ? 0 : p.mu3_mode; key.dev = dev;
+    key.lambda = p.lambda; key.sigma = p.sigma; key.tau = default_tau(eed, p.tau);
+    key.base = ws; key.pitch = L.P;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int victim = 0;
+    for (int i = 0; i < kCache; ++i) {
+        if (g_cache[i].exec && g_cache[i].key == key) {
+            g_cache[i].stamp = ++g_clock;
+            *out = g_cache[i].exec;
+            return FOEED_OK;
+        }
+        if (g_cache[i].stamp < g_cache[victim].stamp) victim = i;
+    }
+    cudaGraphExec_t exec = nullptr;
+    foeed_status st = capture_cycle(eed, d, p, w, h, L, ws, dev, &exec);
+    if (st != FOEED_OK) return st;
+    if (g_cache[victim].exec) cudaGraphExecDestroy(g_cache[victim].exec);
+    g_cache[victim].key = key;
+    g_cache[victim].exec = exec;
+    g_cache[victim].stamp = ++g_clock;
+    *out = exec;
+    return FOEED_OK;
+}
+
+template <typename T>
+cudaError_t launch_prep(const void *f, const uint8_t *mask, void *u_inout, int w, int h, long pitch, const Layout &L,
+                        char *ws, int init_mode, cudaStream_t s)
+{
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    double *partials = reinterpret_cast<double *>(ws + L.partials);
+    uint8_t *mi = reinterpret_cast<uint8_t *>(ws + L.mask);
+    int g = grid_for((long)w * h);
+    prep_kernel<T><<<g, kRedThreads, 0, s>>>(static_cast<const T *>(f), mask, mi, w, h, pitch, L.P, ctl, partials);
+    init_kernel<T><<<g, kRedThreads, 0, s>>>(static_cast<const T *>(f), mi, static_cast<const T *>(u_inout),
+                                             reinterpret_cast<T *>(ws + L.bufC), w, h, pitch, L.P, init_mode, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_out(const Layout &L, char *ws, void *u_inout, int w, int h, long pitch, cudaStream_t s)
+{
+    copy_out_kernel<T><<<grid_for((long)w * h), kRedThreads, 0, s>>>(reinterpret_cast<const T *>(ws + L.bufC),
+                                                                      static_cast<T *>(u_inout), w, h, L.P, pitch);
+    return cudaGetLastError();
+}
+
+foeed_status inpaint(bool eed, const void *f, const uint8_t *mask, void *u_inout, int w, int h, long pitch,
+                     foeed_dtype d, const foeed_params *params, void *workspace, size_t ws_bytes, void *stream,
+                     foeed_report *report)
+{
+    foeed_status st = check_image(w, h, pitch, d);
+    if (st) return st;
+    if ((st = check_params(params, true))) return st;
+    if (!f || !mask || !u_inout || !workspace) return fail(FOEED_ERR_ARG, "NULL data or workspace pointer");
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(FOEED_ERR_ARG, "workspace must be 256-byte aligned");
+    Layout L = layout(w, h, d);
+    if (ws_bytes < L.total) return fail(FOEED_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+    const foeed_params &p = *params;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    Ctl *dctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+
+    cudaGraphExec_t exec = nullptr;
+    if ((st = get_cycle_graph(eed, d, p, w, h, L, ws, &exec))) return st;
+
+    Ctl h0;
+    std::memset(&h0, 0, sizeof(h0));
+    h0.tol = p.tol;
+    CK(cudaMemcpyAsync(dctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaEventRecord(ev0, s));
+    CK(d == FOEED_F64 ? launch_prep<double>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s)
+                      : launch_prep<float>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s));
+    const int every = p.check_every > 0 ? p.check_every : 8;
+    Ctl hc;
+    std::memset(&hc, 0, sizeof(hc));
+    for (int m = 0; m < p.max_cycles; ++m) {
+        CK(cudaGraphLaunch(exec, s));
+        if (p.tol > 0.0 && ((m + 1) % every == 0) && m + 1 < p.max_cycles) {
+            CK(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.done) break;
+        }
+    }
+    CK(d == FOEED_F64 ? launch_copy_out<double>(L, ws, u_inout, w, h, pitch, s)
+                      : launch_copy_out<float>(L, ws, u_inout, w, h, pitch, s));
+    CK(cudaEventRecord(ev1, s));
+    CK(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (report) {
+        report->cycles_run = hc.cycles;
+        report->last_rel_change = hc.last_rel;
+        report->converged = (p.tol > 0.0 && hc.done && !hc.diverged) ? 1 : 0;
+        report->ms = ms;
+    }
+    if (hc.diverged) return fail(FOEED_ERR_DIVERGED, "cycle %d produced a non-finite change", hc.cycles);
+    if (p.tol > 0.0 && !hc.done)
+        return fail(FOEED_ERR_NOT_CONVERGED, "relative change %.3e after %d cycles is not below tol %.3e",
+                    hc.last_rel, hc.cycles, p.tol);
+    g_err[0] = 0;
+    return FOEED_OK;
+}
+
+foeed_status step(bool eed, const void *u_prev, const void *u_cur, void *u_next, const uint8_t *mask, int w, int h,
+                  long pitch, foeed_dtype d, double alpha, const foeed_params *params, void *stream)
+{
+    foeed_status st = check_image(w, h, pitch, d);
+    if (st) return st;
+    if ((st = check_params(params, false))) return st;
+    if (!u_prev || !u_cur || !u_next) return fail(FOEED_ERR_ARG, "NULL image pointer");
+    if (u_next == u_cur) return fail(FOEED_ERR_ARG, "u_next must not alias u_cur");
+    if (!std::isfinite(alpha)) return fail(FOEED_ERR_ARG, "alpha must be finite");
+    StepCall c{};
+    c.uprev = u_prev; c.ucur = u_cur; c.unext = u_next; c.mask = mask;
+    c.w = w; c.h = h; c.pitch = pitch; c.alpha = alpha;
+    c.tau = default_tau(eed, params->tau);
+    c.c0 = nullptr; c.ctl = nullptr; c.partials = nullptr; c.residual = 0; c.check_done = 0;
+    CK(launch_step(eed, d, nullptr, *params, static_cast<cudaStream_t>(stream)));
+    CK(launch_step(eed, d, &c, *params, static_cast<cudaStream_t>(stream)));
+    return FOEED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t foeed_workspace_bytes(int w, int h, foeed_dtype dtype)
+{
+    if (w < 1 || h < 1) return 0;
+    return layout(w, h, dtype).total;
+}
+
+foeed_status foeed_inpaint(const void *f, const uint8_t *mask, void *u_inout, int w, int h, long pitch,
+                           foeed_dtype dtype, const foeed_params *params, void *workspace, size_t workspace_bytes,
+                           void *stream, foeed_report *report)
+{
+    return inpaint(false, f, mask, u_inout, w, h, pitch, dtype, params, workspace, workspace_bytes, stream, report);
+}
+
+foeed_status eed_inpaint(const void *f, const uint8_t *mask, void *u_inout, int w, int h, long pitch,
+                         foeed_dtype dtype, const foeed_params *params, void *workspace, size_t workspace_bytes,
+                         void *stream, foeed_report *report)
+{
+    return inpaint(true, f, mask, u_inout, w, h, pitch, dtype, params, workspace, workspace_bytes, stream, report);
+}
+
+foeed_status foeed_step(const void *u_prev, const void *u_cur, void *u_next, const uint8_t *mask, int w, int h,
+                        long pitch, foeed_dtype dtype, double alpha, const foeed_params *params, void *stream)
+{
+    return step(false, u_prev, u_cur, u_next, mask, w, h, pitch, dtype, alpha, params, stream);
+}
+
+foeed_status eed_step(const void *u_prev, const void *u_cur, void *u_next, const uint8_t *mask, int w, int h,
+                      long pitch, foeed_dtype dtype, double alpha, const foeed_params *params, void *stream)
+{
+    return step(true, u_prev, u_cur, u_next, mask, w, h, pitch, dtype, alpha, params, stream);
+}
+
+size_t foeed_errors_workspace_bytes(int w, int h)
+{
+    (void)w;
+    (void)h;
+    return align_up(sizeof(Ctl), kAlign) + align_up(sizeof(double) * 2 * kRedBlocksMax, kAlign);
+}
+
+foeed_status foeed_errors(const void *u, const void *v, int w, int h, long pitch, foeed_dtype dtype, void *workspace,
+                          size_t workspace_bytes, void *stream, double *out)
+{
+    foeed_status st = check_image(w, h, pitch, dtype);
+    if (st) return st;
+    if (!u || !v || !workspace || !out) return fail(FOEED_ERR_ARG, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(FOEED_ERR_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < foeed_errors_workspace_bytes(w, h)) return fail(FOEED_ERR_ARG, "workspace too small");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws);
+    double *partials = reinterpret_cast<double *>(ws + align_up(sizeof(Ctl), kAlign));
+    CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    int g = grid_for((long)w * h);
+    if (dtype == FOEED_F64)
+        errors_kernel<double><<<g, kRedThreads, 0, s>>>(static_cast<const double *>(u), static_cast<const double *>(v),
+                                                        w, h, pitch, ctl, partials);
+    else
+        errors_kernel<float><<<g, kRedThreads, 0, s>>>(static_cast<const float *>(u), static_cast<const float *>(v), w,
+                                                       h, pitch, ctl, partials);
+    CK(cudaGetLastError());
+    Ctl hc;
+    CK(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out[0] = hc.err[0];
+    out[1] = hc.err[1];
+    out[2] = hc.err[2];
+    return FOEED_OK;
+}
+
+const char *foeed_last_error(void) { return g_err; }
+
+const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

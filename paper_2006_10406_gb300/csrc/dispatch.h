@@ -1,0 +1,21 @@
+// Host-side entry points of the step kernels, one translation unit per
+// (method, storage type) so they compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "foeed_device.cuh"
+
+namespace foeed {
+
+// Output tile of one CTA per storage type (columns x rows).
+constexpr int kTileW32 = 64, kTileH32 = 16;
+constexpr int kTileW64 = 32, kTileH64 = 16;
+
+// Each launches one step on s; a == nullptr only prepares the kernel's attributes.
+cudaError_t step_foeed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
+cudaError_t step_foeed_f64(const StepArgs<double> *a, int R, cudaStream_t s);
+cudaError_t step_eed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
+cudaError_t step_eed_f64(const StepArgs<double> *a, int R, cudaStream_t s);
+
+}  // namespace foeed

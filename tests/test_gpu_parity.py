@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (written per test):
+  FP64 storage: max-abs <= 1e-10 after whole solves, 1e-12 after one step.
+  FP32 storage: max-abs <= 2e-4 on [0, 1] intensities and PSNR difference
+  <= 0.01 dB after whole solves; 2e-5 after one step (float rounding of
+  |tau P u| <= tau * 32 * max|u|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - the marker deselects these on CPU
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2006_10406_gb300 as fg  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    O.set_threads(max(1, min(16, __import__("os").cpu_count() or 1)))
+    yield
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def _psnr(u, ref):
+    mse = float(np.mean((u - ref) ** 2))
+    return math.inf if mse == 0 else 10 * math.log10(1.0 / mse)
+
+
+METHODS = [(0, "foeed"), (1, "eed")]
+
+
+# --------------------------------------------------------------------------
+# single steps, ragged sizes, every Gaussian radius
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("shape", [(37, 53), (1, 7), (6, 1), (2, 2), (64, 64), (67, 130), (17, 200)])
+@pytest.mark.parametrize("sigma", [0.0, 0.5, 1.0, 1.5, 2.0])
+def test_step_f64_matches_oracle(method, shape, sigma):
+    rng = _rng(hash((method, shape, sigma)) % 2 ** 32)
+    h, w = shape
+    ucur = rng.uniform(size=shape)
+    uprev = ucur + 0.01 * rng.normal(size=shape)
+    mask = (rng.uniform(size=shape) < 0.1).astype(np.uint8)
+    alpha, tau, lam = 1.37, (0.05 if method == 0 else 0.25), 0.07
+    ref = O.fsi_step(method, uprev, ucur, mask, alpha, tau, sigma, lam)
+    a, b, m = _dev(uprev, torch.float64), _dev(ucur, torch.float64), _dev(mask, torch.uint8)
+    out = torch.full_like(b, float("nan"))
+    (fg.foeed_step if method == 0 else fg.eed_step)(a, b, out, m, alpha, lam, sigma, tau=tau)
+    got = out.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+    k = mask != 0
+    np.testing.assert_array_equal(got[k], ucur[k])
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("shape", [(37, 53), (64, 64), (67, 130), (3, 300)])
+@pytest.mark.parametrize("sigma", [1.0, 1.5])
+def test_step_f32_matches_oracle(method, shape, sigma):
+    rng = _rng(7 + method)
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    uprev = (ucur + 0.01 * rng.normal(size=shape)).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.1).astype(np.uint8)
+    alpha, tau, lam = 1.2, (0.05 if method == 0 else 0.25), 0.05
+    ref = O.fsi_step(method, uprev, ucur, mask, alpha, tau, sigma, lam)
+    a, b, m = _dev(uprev, torch.float32), _dev(ucur, torch.float32), _dev(mask, torch.uint8)
+    out = torch.empty_like(b)
+    (fg.foeed_step if method == 0 else fg.eed_step)(a, b, out, m, alpha, lam, sigma, tau=tau)
+    got = out.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
+
+
+@pytest.mark.parametrize("g_kind", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("mu3", [0, 1, 2])
+def test_step_variants_f64(g_kind, mu3):
+    rng = _rng(100 + 3 * g_kind + mu3)
+    shape = (33, 41)
+    ucur = rng.uniform(size=shape)
+    mask = (rng.uniform(size=shape) < 0.1).astype(np.uint8)
+    lam = 0.3 if g_kind in (3, 4) else 0.05
+    ref = O.fsi_step(0, ucur, ucur, mask, 2.0 / 3.0, 0.01, 1.0, lam, g_kind, mu3)
+    b, m = _dev(ucur, torch.float64), _dev(mask, torch.uint8)
+    out = torch.empty_like(b)
+    fg.foeed_step(b, b, out, m, 2.0 / 3.0, lam, 1.0, tau=0.01, diffusivity=g_kind, mu3_mode=mu3)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-12)
+
+
+def test_step_without_mask_and_pitched_rows():
+    rng = _rng(9)
+    h, w, pitch = 40, 45, 64
+    base = torch.zeros((h, pitch), dtype=torch.float64, device=DEV)
+    u = base[:, :w]
+    un = torch.zeros((h, pitch), dtype=torch.float64, device=DEV)[:, :w]
+    uc = rng.uniform(size=(h, w))
+    u.copy_(torch.from_numpy(uc))
+    fg.foeed_step(u, u, un, None, 1.0, 0.05, 1.0, tau=0.05)
+    ref = O.fsi_step(0, uc, uc, None, 1.0, 0.05, 1.0, 0.05)
+    np.testing.assert_allclose(un.cpu().numpy(), ref, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# whole solves
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_inpaint_workload1_f64(method):
+    """64x64 FP64, 40 cycles of length 20: max-abs <= 1e-10 against the oracle."""
+    img, mask, p = synth.workload(1)
+    ref, st, info = O.inpaint(method, img, mask, p["sigma"], p["lam"], p["cycle_len"], p["max_cycles"])
+    u, rep = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+        _dev(img, torch.float64), _dev(mask, torch.uint8), p["lam"], p["sigma"], p["cycle_len"], p["max_cycles"])
+    got = u.cpu().numpy()
+    assert rep.cycles_run == p["max_cycles"]
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10)
+    assert abs(rep.last_rel_change - info["rel_change"]) <= 1e-8 * max(info["rel_change"], 1e-300) + 1e-14
+    k = mask != 0
+    np.testing.assert_array_equal(got[k], img[k])
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("dtype", ["f32", "f32_f64u"])
+def test_inpaint_workload1_f32(method, dtype):
+    """Same solve in FP32 storage: max-abs <= 2e-4, PSNR within 0.01 dB of the oracle's."""
+    img, mask, p = synth.workload(1)
+    ref, st, info = O.inpaint(method, img, mask, p["sigma"], p["lam"], p["cycle_len"], p["max_cycles"])
+    f32 = img.astype(np.float32)
+    u, rep = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+        _dev(f32, torch.float32), _dev(mask, torch.uint8), p["lam"], p["sigma"], p["cycle_len"], p["max_cycles"],
+        dtype=dtype)
+    got = u.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 2e-4
+    assert abs(_psnr(got, img) - _psnr(ref, img)) <= 0.01
+    k = mask != 0
+    np.testing.assert_array_equal(u.cpu().numpy()[k], f32[k])
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_inpaint_tol_stops_at_the_oracle_cycle(method):
+    """tol > 0: the device stop flag ends the solve at the same cycle as the oracle."""
+    img, mask, p = synth.workload(2, h=48, w=40)
+    tol = 1e-5
+    ref, st, info = O.inpaint(method, img, mask, 1.0, 0.03, 10, 3000, tol=tol)
+    assert st == 0 and info["converged"]
+    for every in (1, 3, 8):
+        u, rep = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+            _dev(img, torch.float64), _dev(mask, torch.uint8), 0.03, 1.0, 10, 3000, tol=tol, check_every=every)
+        assert rep.converged and rep.cycles_run == info["cycles"]
+        np.testing.assert_allclose(u.cpu().numpy(), ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_inpaint_short_cycles_f64(n):
+    """Cycle lengths 1..4 exercise every buffer-rotation case of the cycle graph."""
+    img, mask, p = synth.workload(1, h=29, w=31)
+    for method in (0, 1):
+        ref, _, _ = O.inpaint(method, img, mask, 1.0, 0.05, n, 5)
+        u, rep = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+            _dev(img, torch.float64), _dev(mask, torch.uint8), 0.05, 1.0, n, 5)
+        assert rep.cycles_run == 5
+        np.testing.assert_allclose(u.cpu().numpy(), ref, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (7, 1), (2, 3), (65, 33)])
+def test_inpaint_tiny_and_ragged_images(shape):
+    rng = _rng(11)
+    img = rng.uniform(size=shape)
+    mask = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    mask.flat[0] = 1
+    for method in (0, 1):
+        ref, _, _ = O.inpaint(method, img, mask, 1.0, 0.1, 5, 4)
+        u, _ = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+            _dev(img, torch.float64), _dev(mask, torch.uint8), 0.1, 1.0, 5, 4)
+        np.testing.assert_allclose(u.cpu().numpy(), ref, rtol=0, atol=1e-11)
+
+
+def test_inpaint_edge_masks():
+    rng = _rng(12)
+    img = rng.uniform(size=(20, 24))
+    # every pixel known: the result is f
+    full = np.ones(img.shape, np.uint8)
+    u, _ = fg.foeed_inpaint(_dev(img, torch.float64), _dev(full, torch.uint8), 0.05, 1.0, 4, 2)
+    np.testing.assert_array_equal(u.cpu().numpy(), img)
+    # no known pixel and init from the mean of an empty set: the zero image stays zero
+    empty = np.zeros(img.shape, np.uint8)
+    u, _ = fg.foeed_inpaint(_dev(img, torch.float64), _dev(empty, torch.uint8), 0.05, 1.0, 4, 2)
+    assert np.all(u.cpu().numpy() == 0.0)
+    # no known pixel, start from u0: the smoothing variant conserves the mean (symmetric P)
+    u, _ = fg.foeed_inpaint(_dev(img, torch.float64), _dev(empty, torch.uint8), 0.05, 1.0, 10, 5, u0=_dev(img, torch.float64))
+    assert abs(u.cpu().numpy().sum() - img.sum()) < 1e-10
+
+
+def test_constant_image_fixed_bitwise_f32():
+    c = np.full((50, 70), 0.3, np.float32)
+    mask = np.zeros(c.shape, np.uint8); mask[5, 5] = 1
+    for m in (0, 1):
+        u, _ = (fg.foeed_inpaint if m == 0 else fg.eed_inpaint)(_dev(c, torch.float32), _dev(mask, torch.uint8),
+                                                               0.05, 1.0, 10, 3)
+        assert np.all(u.cpu().numpy() == np.float32(0.3))
+
+
+def test_host_inputs_round_trip():
+    img, mask, p = synth.workload(1, h=32, w=32)
+    u, rep = fg.foeed_inpaint(img, mask, 0.05, 1.0, 5, 2)
+    assert isinstance(u, torch.Tensor) and not u.is_cuda and u.dtype == torch.float64
+    ref, _, _ = O.inpaint(0, img, mask, 1.0, 0.05, 5, 2)
+    np.testing.assert_allclose(u.numpy(), ref, rtol=0, atol=1e-11)
+
+
+def test_divergence_and_argument_errors():
+    rng = _rng(13)
+    img = rng.uniform(size=(16, 16))
+    empty = np.zeros(img.shape, np.uint8)
+    u, rep = fg.foeed_inpaint(_dev(img, torch.float64), _dev(empty, torch.uint8), 1e30, 1.0, 1, 400, tau=0.5,
+                              u0=_dev(img, torch.float64), raise_on_status=False)
+    assert rep.status == 4
+    with pytest.raises(fg.FoeedError):
+        fg.foeed_inpaint(_dev(img, torch.float64), _dev(empty, torch.uint8), -1.0, 1.0, 1, 1)
+    with pytest.raises(fg.FoeedError):
+        fg.foeed_inpaint(_dev(img, torch.float64), _dev(empty, torch.uint8), 0.1, 2.5, 1, 1)
+    b = _dev(img, torch.float64)
+    with pytest.raises(fg.FoeedError):
+        fg.foeed_step(b, b, b, None, 1.0, 0.1, 1.0)
+
+
+def test_errors_metric():
+    rng = _rng(14)
+    a = rng.uniform(size=(31, 45)); b = rng.uniform(size=(31, 45))
+    mse, aae, psnr = fg.foeed_errors(_dev(a, torch.float64), _dev(b, torch.float64))
+    rm, ra = O.errors(a, b)
+    assert abs(mse - rm) < 1e-14 and abs(aae - ra) < 1e-14
+    assert abs(psnr - 10 * math.log10(1 / rm)) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# full sizes, in the launch configuration the benchmark times
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_fullsize_2048_one_cycle_f32_vs_oracle(method):
+    """2048 x 2048 phantom, sigma 1.5 (R = 5), one FSI cycle of length 40, every pixel."""
+    img, mask, p = synth.workload(3)
+    f32 = img.astype(np.float32)
+    ref, _, _ = O.inpaint(method, f32.astype(np.float64), mask, p["sigma"], p["lam"], p["cycle_len"], 1)
+    u, rep = (fg.foeed_inpaint if method == 0 else fg.eed_inpaint)(
+        _dev(f32, torch.float32), _dev(mask, torch.uint8), p["lam"], p["sigma"], p["cycle_len"], 1)
+    got = u.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 2e-4
+
+
+def test_fullsize_2048_bench_solve_properties():
+    """The benchmarked solve (100 cycles of 40): Dirichlet pixels exact, finite,
+    and the FP32 result within 2e-4 of the FP64 GPU result."""
+    img, mask, p = synth.workload(3)
+    f32 = img.astype(np.float32)
+    u32, r32 = fg.foeed_inpaint(_dev(f32, torch.float32), _dev(mask, torch.uint8), p["lam"], p["sigma"],
+                                p["cycle_len"], p["max_cycles"])
+    u64, r64 = fg.foeed_inpaint(_dev(f32.astype(np.float64), torch.float64), _dev(mask, torch.uint8), p["lam"],
+                                p["sigma"], p["cycle_len"], p["max_cycles"])
+    a, b = u32.cpu().numpy(), u64.cpu().numpy()
+    assert r32.cycles_run == r64.cycles_run == p["max_cycles"]
+    assert np.isfinite(a).all()
+    k = mask != 0
+    np.testing.assert_array_equal(a[k], f32[k])
+    assert np.max(np.abs(a.astype(np.float64) - b)) <= 2e-4
+    assert abs(_psnr(a.astype(np.float64), img) - _psnr(b, img)) <= 0.01
