@@ -39,12 +39,13 @@ WORKLOAD = 3
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel on the full 2048x2048 workload, and the hash of the
 # kernel source it was taken on; reported only while the source is unchanged.
-NCU_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"source_sha1": "489d1b691f0936910cb573070c5f5e12233bfcbc",
+               "bytes_per_launch": 37788928 + 40448}  # profiles/fsi_step_fast_foeed_f32_r5_2048x2048.md
 
 
 def kernel_source_sha1():
     h = hashlib.sha1()
-    for fn in ("step_kernel.cuh", "foeed_device.cuh", "dispatch.h"):
+    for fn in ("step_fast.cuh", "foeed_device.cuh", "dispatch.h"):
         with open(os.path.join(ROOT, "paper_2006_10406_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -114,6 +115,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def instance_for_rank(rank: int) -> int:
+    """Each rank solves its own independent instance of the workload (seeded by rank)."""
+    return rank
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """Slowest rank's value (all ranks must call it); identity without a process group."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -177,6 +193,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--minimal", action="store_true",
+                    help="only the warm-up and timed solves (for profiler launch lists)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -197,7 +215,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    img, mask, p = synth.workload(WORKLOAD, instance=rank)
+    img, mask, p = synth.workload(WORKLOAD, instance=instance_for_rank(rank))
     W, H, n, cycles = p["w"], p["h"], p["cycle_len"], p["max_cycles"]
     f32 = img.astype(np.float32)
     fd = torch.from_numpy(f32).to(dev)
@@ -228,16 +246,21 @@ def main():
     if pg:
         pg.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_total = sum(ms)
-    if pg:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(sum(ms), pg, dev)
     ms_per_step = ms_total / args.steps
     pu_per_solve = W * H * cycles * n
     value = pu_per_solve * world / (ms_per_step / 1e3)
     launches_per_solve = 2 + cycles * n + 1
     clocks = clk.summary()
+
+    if args.minimal:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                              "minimal": True}), flush=True)
+        if pg:
+            pg.destroy_process_group()
+        return
 
     # ---- end to end: host buffers, copies inside the timed region ----
     fh = torch.from_numpy(f32).pin_memory()
@@ -266,7 +289,7 @@ def main():
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha1"] == kernel_source_sha1() else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "fsi_step_kernel<float,float,5,64,16,FOEED>",
+                "kernel": "fsi_step_fast<R=5, FOEED, float>",
                 "algorithmic_bytes_per_launch": BYTES_PER_PIXEL_UPDATE * W * H}
 
     extra = {}

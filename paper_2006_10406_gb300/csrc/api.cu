@@ -232,6 +232,11 @@ StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
     a.alpha = c.alpha;
     a.tau = c.tau;
     a.lambda = p.lambda;
+    a.alpha_t = T(c.alpha);
+    a.tau_t = T(c.tau);
+    a.l2 = T(p.lambda * p.lambda);
+    a.inv_l2 = T(1.0 / (p.lambda * p.lambda));
+    a.c4 = T(0.25 / (p.lambda * p.lambda));
     a.g_kind = p.diffusivity;
     a.mu3_mode = p.mu3_mode;
     gauss_taps<T>(p.sigma, a.wts);
@@ -240,6 +245,21 @@ StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
     a.residual = c.residual;
     a.check_done = c.check_done;
     return a;
+}
+
+// The register-blocked FP32 kernel covers the paper's configuration
+// (Charbonnier g; mu3 = sqrt(mu1) for FOEED); other variants use the generic one.
+bool fast_params(bool eed, const foeed_params &p) { return p.diffusivity == 0 && (eed || p.mu3_mode == 0); }
+
+bool aligned16(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+bool fast_eligible(bool eed, const StepCall &c, const foeed_params &p)
+{
+    if (!fast_params(eed, p) || c.pitch % 4 != 0) return false;
+    if (!aligned16(c.uprev) || !aligned16(c.ucur) || !aligned16(c.unext)) return false;
+    if (c.mask && !aligned16(c.mask)) return false;
+    if (c.residual && !aligned16(c.c0)) return false;
+    return true;
 }
 
 // c == nullptr: only prepare the kernel (shared-memory attribute), no launch.
@@ -254,6 +274,11 @@ cudaError_t launch_step(bool eed, foeed_dtype d, const StepCall *c, const foeed_
     StepArgs<float> a;
     if (c) a = make_args<float>(*c, p);
     bool f64u = d == FOEED_F32_F64U;
+    if (c ? fast_eligible(eed, *c, p) : fast_params(eed, p)) {
+        cudaError_t e = eed ? step_fast_eed_f32(c ? &a : nullptr, R, f64u, s)
+                            : step_fast_foeed_f32(c ? &a : nullptr, R, f64u, s);
+        if (c || e != cudaSuccess) return e;  // when preparing, also prepare the generic kernel
+    }
     return eed ? step_eed_f32(c ? &a : nullptr, R, f64u, s) : step_foeed_f32(c ? &a : nullptr, R, f64u, s);
 }
 
@@ -541,3 +566,4 @@ const char *foeed_last_error(void) { return g_err; }
 const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+

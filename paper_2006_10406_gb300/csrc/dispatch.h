@@ -18,4 +18,10 @@ cudaError_t step_foeed_f64(const StepArgs<double> *a, int R, cudaStream_t s);
 cudaError_t step_eed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
 cudaError_t step_eed_f64(const StepArgs<double> *a, int R, cudaStream_t s);
 
+// Register-blocked FP32 kernels (64 x 32 tiles): Charbonnier g, FOEED with
+// mu3 = sqrt(mu1); need a row pitch that is a multiple of 4 elements and
+// 16-byte aligned image and mask pointers.
+cudaError_t step_fast_foeed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
+cudaError_t step_fast_eed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
+
 }  // namespace foeed

@@ -50,6 +50,10 @@ struct StepArgs {
     double alpha; // FSI extrapolation weight
     double tau;
     double lambda;
+    // the same constants pre-rounded to T on the host (no per-thread FP64 work)
+    T alpha_t, tau_t;
+    T l2, inv_l2;  // lambda^2, 1/lambda^2
+    T c4;          // 1/(4 lambda^2): lambda1/lambda^2 = |2 grad u_sigma|^2 * c4
     int g_kind, mu3_mode;
     T wts[2 * kRMax + 1];
     Ctl *ctl;            // null outside an inpaint solve

@@ -1,0 +1,27 @@
+// Instantiations of the register-blocked FP32 step: EED (Charbonnier g).
+#include "dispatch.h"
+#include "step_fast.cuh"
+
+namespace foeed {
+
+template <typename U>
+static cudaError_t run(const StepArgs<float> *a, int R, cudaStream_t s)
+{
+    switch (R) {
+    case 0: return launch_fsi_step_fast<0, true, U>(a, s);
+    case 1: return launch_fsi_step_fast<1, true, U>(a, s);
+    case 2: return launch_fsi_step_fast<2, true, U>(a, s);
+    case 3: return launch_fsi_step_fast<3, true, U>(a, s);
+    case 4: return launch_fsi_step_fast<4, true, U>(a, s);
+    case 5: return launch_fsi_step_fast<5, true, U>(a, s);
+    case 6: return launch_fsi_step_fast<6, true, U>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t step_fast_eed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s)
+{
+    return f64_update ? run<double>(a, R, s) : run<float>(a, R, s);
+}
+
+}  // namespace foeed

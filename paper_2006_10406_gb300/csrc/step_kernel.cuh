@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(kThreads) fsi_step_kernel(const StepArgs<T> p)
     __shared__ double red[64];
 
     if (p.check_done && p.ctl->done) return;
+    // alpha and tau in the update type: the pre-rounded copies when U == T
+    const U alpha = sizeof(U) == sizeof(T) ? U(p.alpha_t) : U(p.alpha);
+    const U tau = sizeof(U) == sizeof(T) ? U(p.tau_t) : U(p.tau);
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
@@ -77,8 +80,8 @@ __global__ void __launch_bounds__(kThreads) fsi_step_kernel(const StepArgs<T> p)
     __syncthreads();
 
     // ---- D: tensor and inner derivatives on tile+-1 ----
-    const T l2 = T(p.lambda * p.lambda);
-    const T inv_l2 = T(1.0 / (p.lambda * p.lambda));
+    const T l2 = p.l2;
+    const T inv_l2 = p.inv_l2;
     constexpr int PL = G::ST_W * G::ST_H;
     for (int i = tid; i < PL; i += kThreads) {
         int r = i / G::ST_W, c = i - r * G::ST_W;
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(kThreads) fsi_step_kernel(const StepArgs<T> p)
             un = uc;
         } else {
             U up = U(p.uprev[gi]);
-            U ex = U(uc) - U(p.tau) * U(Pu);  // (I - tau P) u^k
-            un = T(up + U(p.alpha) * (ex - up));
+            U ex = U(uc) - tau * U(Pu);  // (I - tau P) u^k
+            un = T(up + alpha * (ex - up));
         }
         if (p.residual) {
             double d = double(un) - double(p.c0[gi]);

@@ -278,3 +278,50 @@ def test_fullsize_2048_bench_solve_properties():
     np.testing.assert_array_equal(a[k], f32[k])
     assert np.max(np.abs(a.astype(np.float64) - b)) <= 2e-4
     assert abs(_psnr(a.astype(np.float64), img) - _psnr(b, img)) <= 0.01
+
+
+# --------------------------------------------------------------------------
+# the register-blocked FP32 kernel (pitch % 4 == 0, Charbonnier) and the
+# generic one (any pitch, every diffusivity / mu3) must agree with the oracle
+
+def _pitched(a, pitch, dtype):
+    h, w = a.shape
+    buf = torch.zeros((h, pitch), dtype=dtype, device=DEV)
+    buf[:, :w] = torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+    return buf[:, :w]
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("shape", [(100, 130), (33, 70), (64, 64), (5, 300), (130, 7)])
+@pytest.mark.parametrize("sigma", [0.5, 1.0, 1.5, 2.0])
+def test_fast_and_generic_f32_paths_match_oracle(method, shape, sigma):
+    rng = _rng(200 + method)
+    h, w = shape
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    uprev = (ucur + 0.01 * rng.normal(size=shape)).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.08).astype(np.uint8)
+    alpha, tau, lam = 1.5, (0.05 if method == 0 else 0.25), 0.03
+    ref = O.fsi_step(method, uprev, ucur, mask, alpha, tau, sigma, lam)
+    outs = []
+    for pitch in (((w + 3) // 4) * 4 + 4, w + 1 if (w + 1) % 4 else w + 2):
+        a, b = _pitched(uprev, pitch, torch.float32), _pitched(ucur, pitch, torch.float32)
+        m = _pitched(mask, pitch, torch.uint8)
+        out = _pitched(np.zeros(shape), pitch, torch.float32)
+        (fg.foeed_step if method == 0 else fg.eed_step)(a, b, out, m, alpha, lam, sigma, tau=tau)
+        outs.append(out.cpu().numpy().astype(np.float64))
+    for got in outs:
+        np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
+        np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
+
+
+@pytest.mark.parametrize("g_kind,mu3", [(1, 0), (2, 1), (0, 2), (0, 1)])
+def test_generic_f32_variants(g_kind, mu3):
+    rng = _rng(300 + g_kind)
+    shape = (48, 64)
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.1).astype(np.uint8)
+    ref = O.fsi_step(0, ucur, ucur, mask, 2.0 / 3.0, 0.05, 1.0, 0.05, g_kind, mu3)
+    b, m = _dev(ucur, torch.float32), _dev(mask, torch.uint8)
+    out = torch.empty_like(b)
+    fg.foeed_step(b, b, out, m, 2.0 / 3.0, 0.05, 1.0, tau=0.05, diffusivity=g_kind, mu3_mode=mu3)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=2e-5)
