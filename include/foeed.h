@@ -145,6 +145,33 @@ size_t foeed_errors_workspace_bytes(int w, int h);
 foeed_status foeed_errors(const void *u, const void *v, int w, int h, long pitch, foeed_dtype dtype,
                           void *workspace, size_t workspace_bytes, void *stream, double *out);
 
+/*
+ * FOEED solve for callers that cannot allocate device memory (no cudaMalloc,
+ * no workspace of their own): code living inside another framework's memory
+ * arena, plug-ins that must not touch the device heap, or latency-critical
+ * paths where an allocation may block or fail. The paper has no counterpart;
+ * this is a deployment variant of foeed_inpaint.
+ *   Same arguments and result as foeed_inpaint, without the workspace: the
+ *   scratch lives in one static device array of FOEED_STATIC_SCRATCH_BYTES
+ *   (64 MiB) that every device loading the library keeps until the process
+ *   exits. Images whose foeed_workspace_bytes(w, h, dtype) exceed it are
+ *   rejected with FOEED_ERR_ARG (square images up to 2269 x 2269 in FP32,
+ *   1632 x 1632 in FP64).
+ *   The call allocates nothing: no cudaMalloc / cudaFree, no graph, no event;
+ *   it launches the step kernels one by one on `stream`.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture. All calls on a device share the one array and
+ *   it keeps the previous call's contents (the solve re-initialises what it
+ *   reads), so calls that overlap on the GPU (other streams, other threads)
+ *   race: serialise them. report->ms is host wall time of the call.
+ */
+#define FOEED_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+size_t foeed_static_scratch_bytes(void);
+foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask, void *u_inout, int w, int h,
+                                  long pitch, foeed_dtype dtype, const foeed_params *params, void *stream,
+                                  foeed_report *report);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *foeed_last_error(void);
 

@@ -8,6 +8,7 @@
 // every few cycles.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -567,3 +568,123 @@ const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Solver entry point that allocates nothing.
+//
+// Some callers cannot call cudaMalloc at all: code that runs inside another
+// framework's allocator arena, plug-ins that may not touch the device heap, or
+// real-time paths where an allocation could block or fail. For them,
+// foeed_inpaint_static runs the FP32/FP64 FOEED solve with its scratch (the
+// control block, reduction partials, three image buffers and the internal
+// mask) in one file-scope device array of fixed size instead of a caller
+// workspace. Every device that loads this library holds that array until the
+// process exits. The solve uses plain stream-ordered kernel launches: no graph,
+// no event, no allocation of any kind.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[FOEED_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+unsigned char *g_static_ptr[64] = {};
+
+// Device address of the static scratch on the current device, looked up once
+// per device (host code only sees a host-side stand-in for the symbol).
+foeed_status static_scratch(unsigned char **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(FOEED_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return fail(FOEED_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_static_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return FOEED_OK;
+}
+
+}  // namespace
+
+extern "C" size_t foeed_static_scratch_bytes(void) { return FOEED_STATIC_SCRATCH_BYTES; }
+
+extern "C" foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask, void *u_inout, int w, int h,
+                                             long pitch, foeed_dtype dtype, const foeed_params *params,
+                                             void *stream, foeed_report *report)
+{
+    foeed_status st = check_image(w, h, pitch, dtype);
+    if (st) return st;
+    if ((st = check_params(params, true))) return st;
+    if (!f || !mask || !u_inout) return fail(FOEED_ERR_ARG, "NULL data pointer");
+    const Layout L = layout(w, h, dtype);
+    if (L.total > FOEED_STATIC_SCRATCH_BYTES)
+        return fail(FOEED_ERR_ARG, "image needs %zu bytes of scratch, more than the static %zu bytes", L.total,
+                    (size_t)FOEED_STATIC_SCRATCH_BYTES);
+    unsigned char *base = nullptr;
+    if ((st = static_scratch(&base))) return st;
+    char *ws = reinterpret_cast<char *>(base);
+    const foeed_params &p = *params;
+    const bool eed = false;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctl *dctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    double *partials = reinterpret_cast<double *>(ws + L.partials);
+    const uint8_t *mi = reinterpret_cast<const uint8_t *>(ws + L.mask);
+    void *C = ws + L.bufC, *A = ws + L.bufA, *B = ws + L.bufB;
+    void *buf[2] = {A, B};
+    const int n = p.cycle_len;
+    const double tau = default_tau(eed, p.tau);
+    const size_t img_bytes = (size_t)h * L.P * elem_size(dtype);
+    const auto t0 = std::chrono::steady_clock::now();
+
+    // the control block must start from zero (ticket, flags, counters)
+    Ctl h0;
+    std::memset(&h0, 0, sizeof(h0));
+    h0.tol = p.tol;
+    CK(cudaMemcpyAsync(dctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(launch_step(eed, dtype, nullptr, p, s));
+    CK(dtype == FOEED_F64 ? launch_prep<double>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s)
+                          : launch_prep<float>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s));
+    const int every = p.check_every > 0 ? p.check_every : 8;
+    Ctl hc;
+    std::memset(&hc, 0, sizeof(hc));
+    for (int m = 0; m < p.max_cycles; ++m) {
+        for (int k = 0; k < n; ++k) {  // the same buffer rotation as the captured cycle
+            StepCall c{};
+            c.w = w; c.h = h; c.pitch = L.P; c.mask = mi;
+            c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
+            c.tau = tau;
+            c.ctl = dctl; c.partials = partials; c.check_done = 1;
+            const bool last = (k == n - 1);
+            if (k == 0) { c.uprev = C; c.ucur = C; c.unext = A; }
+            else if (k == 1) { c.uprev = C; c.ucur = A; c.unext = last ? C : B; }
+            else { c.uprev = buf[k % 2]; c.ucur = buf[(k + 1) % 2]; c.unext = last ? C : buf[k % 2]; }
+            if (last) { c.residual = 1; c.c0 = C; }
+            CK(launch_step(eed, dtype, &c, p, s));
+            if (last && n == 1) CK(cudaMemcpyAsync(C, A, img_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        if (p.tol > 0.0 && ((m + 1) % every == 0) && m + 1 < p.max_cycles) {
+            CK(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.done) break;
+        }
+    }
+    CK(dtype == FOEED_F64 ? launch_copy_out<double>(L, ws, u_inout, w, h, pitch, s)
+                          : launch_copy_out<float>(L, ws, u_inout, w, h, pitch, s));
+    CK(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const auto t1 = std::chrono::steady_clock::now();
+    if (report) {
+        report->cycles_run = hc.cycles;
+        report->last_rel_change = hc.last_rel;
+        report->converged = (p.tol > 0.0 && hc.done && !hc.diverged) ? 1 : 0;
+        report->ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
+    }
+    if (hc.diverged) return fail(FOEED_ERR_DIVERGED, "cycle %d produced a non-finite change", hc.cycles);
+    if (p.tol > 0.0 && !hc.done)
+        return fail(FOEED_ERR_NOT_CONVERGED, "relative change %.3e after %d cycles is not below tol %.3e",
+                    hc.last_rel, hc.cycles, p.tol);
+    g_err[0] = 0;
+    return FOEED_OK;
+}
