@@ -62,10 +62,12 @@ _lib = None
 
 
 def lib():
-    """Load libfoeed_gb300.so (building it with nvcc if it is missing or stale)."""
+    """Load libfoeed_gb300.so (building it with nvcc if it is missing or stale).
+
+    FOEED_LIBRARY, if set, names another build of the same library to load."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("FOEED_LIBRARY") or _build.build()
         L = C.CDLL(path)
         vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
         L.foeed_workspace_bytes.argtypes = [i, i, i]

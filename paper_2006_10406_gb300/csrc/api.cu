@@ -216,6 +216,7 @@ struct StepCall {
     Ctl *ctl;
     double *partials;
     int residual, check_done;
+    int pdl;  // launch with a programmatic dependency on the previous kernel
 };
 
 template <typename T>
@@ -245,6 +246,7 @@ StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
     a.partials = c.partials;
     a.residual = c.residual;
     a.check_done = c.check_done;
+    a.pdl = c.pdl;
     return a;
 }
 
@@ -337,6 +339,7 @@ foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w
         else if (k == 1) { c.uprev = C; c.ucur = A; c.unext = last ? C : B; }
         else { c.uprev = buf[k % 2]; c.ucur = buf[(k + 1) % 2]; c.unext = last ? C : buf[k % 2]; }
         if (last) { c.residual = 1; c.c0 = C; }
+        c.pdl = k > 0 ? 1 : 0;  // successive steps overlap launch and tail (programmatic dependency)
         err = launch_step(eed, d, &c, p, cs);
         if (err == cudaSuccess && last && n == 1) err = cudaMemcpyAsync(C, A, img_bytes, cudaMemcpyDeviceToDevice, cs);
     }

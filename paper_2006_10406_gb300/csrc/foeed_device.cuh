@@ -60,7 +60,31 @@ struct StepArgs {
     double *partials;    // per-block residual partials
     int residual;        // 1: accumulate the cycle residual and finalise it
     int check_done;      // 1: return at once when ctl->done is set
+    int pdl;             // host only: launch with programmatic dependency on the previous kernel
 };
+
+// Launches kern over grid with the arguments a, as an ordinary launch or, when
+// a.pdl is set, with programmatic stream serialisation (the kernel waits for
+// its predecessor with griddepcontrol.wait).
+template <typename Kern, typename Args>
+cudaError_t launch_step_kernel(Kern kern, dim3 grid, int threads, size_t smem, cudaStream_t s, const Args &a)
+{
+    if (!a.pdl) {
+        kern<<<grid, threads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
 
 __device__ __forceinline__ int mirror_idx(int i, int n)
 {

@@ -66,7 +66,12 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
     float *ss = sx + G::SXT;
     __shared__ double red[64];
 
+    // Programmatic dependent launch: wait until the previous step's grid has
+    // completed and its writes are visible (a no-op for an ordinary launch),
+    // then let the next step's CTAs be scheduled as SM slots free up.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (p.check_done && p.ctl->done) return;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const U alpha = sizeof(U) == sizeof(float) ? U(p.alpha_t) : U(p.alpha);
     const U tau = sizeof(U) == sizeof(float) ? U(p.tau_t) : U(p.tau);
 
@@ -419,8 +424,7 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
     auto kern = fsi_step_fast<R, EED, U>;
     if (!ap) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     dim3 grid((ap->w + G::TW - 1) / G::TW, (ap->h + G::TH - 1) / G::TH);
-    kern<<<grid, 256, G::SMEM, s>>>(*ap);
-    return cudaGetLastError();
+    return launch_step_kernel(kern, grid, 256, G::SMEM, s, *ap);
 }
 
 }  // namespace foeed

@@ -33,7 +33,12 @@ __global__ void __launch_bounds__(kThreads) fsi_step_kernel(const StepArgs<T> p)
     T *st = ss + G::SS_W * G::SS_H;
     __shared__ double red[64];
 
+    // Programmatic dependent launch: wait until the previous step's grid has
+    // completed and its writes are visible (a no-op for an ordinary launch),
+    // then let the next step's CTAs be scheduled as SM slots free up.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (p.check_done && p.ctl->done) return;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // alpha and tau in the update type: the pre-rounded copies when U == T
     const U alpha = sizeof(U) == sizeof(T) ? U(p.alpha_t) : U(p.alpha);
     const U tau = sizeof(U) == sizeof(T) ? U(p.tau_t) : U(p.tau);
@@ -193,8 +198,7 @@ cudaError_t launch_fsi_step(const StepArgs<T> *ap, cudaStream_t s)
     if (!ap) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const StepArgs<T> &a = *ap;
     dim3 grid((a.w + TW - 1) / TW, (a.h + TH - 1) / TH);
-    kern<<<grid, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_step_kernel(kern, grid, kThreads, smem, s, a);
 }
 
 }  // namespace foeed
