@@ -185,6 +185,45 @@ def cpu_baseline_leg(p, img, mask):
                       f"{dt:.1f} s"}
 
 
+def batched_leg(fg, synth, torch, dev, stream):
+    """W4: 256 piecewise-smooth images of uneven sizes (sides 128..1024, square and
+    2:1, mask density 2-10%, lambda 0.01-0.1), sigma 1, 50 FSI cycles of length 25,
+    solved in one launch per step over all tiles, against solving them one by one."""
+    import numpy as np
+    cases = synth.batched_workload(256)
+    imgs = [torch.from_numpy(c[0].astype(np.float32)).to(dev) for c in cases]
+    masks = [torch.from_numpy(c[1]).to(dev) for c in cases]
+    lams = [float(c[2]) for c in cases]
+    n, cycles = 25, 50
+    pixels = sum(int(im.numel()) for im in imgs)
+    pu = pixels * n * cycles
+    outs, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, cycles)  # warm-up
+    ws = torch.empty(fg.workspace_bytes(1024, 1024, fg.F32), dtype=torch.uint8, device=dev)
+    times = []
+    for _ in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        outs, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, cycles, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(a.elapsed_time(b))
+    for f, m, lam in zip(imgs[:4], masks[:4], lams[:4]):  # warm the single-image path
+        fg.foeed_inpaint(f, m, lam, 1.0, n, 1, workspace=ws)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    diff = 0.0
+    for f, m, lam, u in zip(imgs, masks, lams, outs):
+        ref, _ = fg.foeed_inpaint(f, m, lam, 1.0, n, cycles, workspace=ws, stream=stream)
+        diff = max(diff, float((ref - u).abs().max().item()))
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = a.elapsed_time(b)
+    ms = min(times)
+    return {"value": pu / (ms / 1e3), "unit": UNIT, "images": len(imgs), "pixels": pixels, "ms_per_solve": ms,
+            "one_by_one_value": pu / (seq_ms / 1e3), "one_by_one_ms": seq_ms,
+            "max_abs_diff_vs_one_by_one": diff, "fsi_cycles": cycles, "cycle_len": n}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +232,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--minimal", action="store_true",
                     help="only the warm-up and timed solves (for profiler launch lists)")
     args = ap.parse_args()
@@ -317,6 +357,9 @@ def main():
             extra["accuracy"] = {"max_abs_f32_vs_f64_gpu": diff, "psnr_f32_db": m32[2], "psnr_f64_db": m64[2],
                                  "psnr_delta_db": abs(m32[2] - m64[2]), "mse_f32": m32[0], "mse_f64": m64[0]}
             del ws64
+
+    if rank == 0 and not args.no_batched:
+        extra["batched"] = batched_leg(fg, synth, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -132,6 +132,36 @@ foeed_status eed_step(const void *u_prev, const void *u_cur, void *u_next, const
                       int w, int h, long pitch, foeed_dtype dtype, double alpha,
                       const foeed_params *params, void *stream);
 
+/* One image of a batched solve: device pointers and sizes as for foeed_inpaint,
+ * with its own contrast parameter lambda. */
+typedef struct {
+    const void *f;         /* [h x pitch] known grey values */
+    const uint8_t *mask;   /* [h x pitch] nonzero = known pixel */
+    void *u_inout;         /* [h x pitch] result (read on entry if init_mode == 1) */
+    int w, h;
+    long pitch;            /* elements (bytes for the mask) */
+    double lambda;         /* contrast parameter of this image (> 0) */
+} foeed_instance;
+
+/* Workspace bytes foeed_inpaint_batch needs for these images. */
+size_t foeed_batch_workspace_bytes(const foeed_instance *inst, int count, foeed_dtype dtype);
+
+/*
+ * Many FOEED inpainting problems of uneven sizes solved together: every FSI
+ * step is one kernel launch over the tiles of all images (a work list of
+ * (image, tile) pairs), one FSI cycle is one captured CUDA graph, each image
+ * keeps its own lambda, mask, buffers, cycle residual and stop flag. Each
+ * image's result equals foeed_inpaint on that image alone (the same tile
+ * arithmetic). Supports FOEED_F32 / FOEED_F32_F64U with the Charbonnier
+ * diffusivity and mu3 = sqrt(mu1) (the paper's configuration), cycle_len >= 2;
+ * params->lambda is ignored (each image has its own). inst is a host array;
+ * reports (count entries) may be NULL. Returns the first non-OK status of any
+ * image (FOEED_ERR_NOT_CONVERGED / FOEED_ERR_DIVERGED), else FOEED_OK.
+ */
+foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
+                                 const foeed_params *params, void *workspace, size_t workspace_bytes,
+                                 void *stream, foeed_report *reports);
+
 /* Bytes of workspace foeed_errors needs for a w x h image. */
 size_t foeed_errors_workspace_bytes(int w, int h);
 

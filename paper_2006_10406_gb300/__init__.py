@@ -22,7 +22,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_step", "eed_step", "foeed_errors", "workspace_bytes",
+__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "foeed_step", "eed_step", "foeed_errors",
+           "workspace_bytes",
            "Report", "FoeedError", "lib", "F32", "F64", "F32_F64U", "STATUS"]
 
 F32, F64, F32_F64U = 0, 1, 2
@@ -42,6 +43,11 @@ class _Params(C.Structure):
                 ("cycle_len", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double),
                 ("diffusivity", C.c_int), ("mu3_mode", C.c_int), ("init_mode", C.c_int),
                 ("check_every", C.c_int)]
+
+
+class _Instance(C.Structure):
+    _fields_ = [("f", C.c_void_p), ("mask", C.c_void_p), ("u_inout", C.c_void_p), ("w", C.c_int), ("h", C.c_int),
+                ("pitch", C.c_long), ("lambda_", C.c_double)]
 
 
 class _Report(C.Structure):
@@ -80,6 +86,11 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, vp, i, i, C.c_long, i, d, C.POINTER(_Params), vp]
             fn.restype = i
+        L.foeed_batch_workspace_bytes.argtypes = [C.POINTER(_Instance), i, i]
+        L.foeed_batch_workspace_bytes.restype = sz
+        L.foeed_inpaint_batch.argtypes = [C.POINTER(_Instance), i, i, C.POINTER(_Params), vp, sz, vp,
+                                          C.POINTER(_Report)]
+        L.foeed_inpaint_batch.restype = i
         L.foeed_errors_workspace_bytes.argtypes = [i, i]
         L.foeed_errors_workspace_bytes.restype = sz
         L.foeed_errors.argtypes = [vp, vp, i, i, C.c_long, i, vp, sz, vp, C.POINTER(C.c_double)]
@@ -209,6 +220,49 @@ def foeed_inpaint(f, mask, lam, sigma, cycle_len, max_cycles, **kw):
 def eed_inpaint(f, mask, lam, sigma, cycle_len, max_cycles, **kw):
     """Second-order EED solve (Eq. EEDModel), same arguments as foeed_inpaint (tau <= 0: 0.25)."""
     return _inpaint(1, f, mask, lam, sigma, cycle_len, max_cycles, **kw)
+
+
+def foeed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, tau=0.0, tol=0.0, init_mode=0,
+                        dtype="f32", check_every=8, stream=None, workspace=None, raise_on_status=True):
+    """Batched FOEED solve of many images of uneven sizes (one launch per FSI step over
+    all their tiles, one captured graph per cycle). images/masks: lists of 2-D CUDA
+    tensors (float32 / uint8, unit column stride); lambdas: one contrast parameter per
+    image. Returns (list of result tensors, list of Report)."""
+    torch = _torch()
+    count = len(images)
+    if not (len(masks) == len(lambdas) == count) or count == 0:
+        raise FoeedError(1, "images, masks and lambdas must have the same nonzero length")
+    code = _dtype_code(None, dtype)
+    dev = images[0].device
+    outs, arr = [], (_Instance * count)()
+    keep = []
+    for i, (f, m, lam) in enumerate(zip(images, masks, lambdas)):
+        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dim() == 2 and f.dtype == torch.float32):
+            raise FoeedError(1, f"image {i} must be a 2-D float32 CUDA tensor")
+        if f.stride(1) != 1:
+            f = f.contiguous()
+        h, w = f.shape
+        pitch = f.stride(0)
+        m = m if (m.is_cuda and m.dtype == torch.uint8 and m.stride(1) == 1 and m.stride(0) == pitch) \
+            else _pitched_like(m.to(dev, torch.uint8), pitch)
+        u = torch.empty_strided((h, w), (pitch, 1), dtype=torch.float32, device=dev)
+        keep += [f, m]
+        outs.append(u)
+        arr[i] = _Instance(f.data_ptr(), m.data_ptr(), u.data_ptr(), w, h, pitch, float(lam))
+    nbytes = int(lib().foeed_batch_workspace_bytes(arr, count, code))
+    if nbytes == 0:
+        raise FoeedError(1, "invalid batch")
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    p = _params(1.0, sigma, tau, cycle_len, max_cycles, tol, 0, 0, init_mode, check_every)
+    reps = (_Report * count)()
+    with torch.cuda.device(dev):
+        st = lib().foeed_inpaint_batch(arr, count, code, C.byref(p), C.c_void_p(workspace.data_ptr()),
+                                       workspace.numel(), _stream_ptr(stream), reps)
+    if st not in (0, 3, 4) or (raise_on_status and st != 0):
+        _check(st)
+    reports = [Report(st, r.cycles_run, r.last_rel_change, bool(r.converged), r.ms) for r in reps]
+    return outs, reports
 
 
 def _step(method, u_prev, u_cur, u_next, mask, alpha, lam, sigma, tau=0.0, diffusivity=0, mu3_mode=0,

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "dispatch.h"
 #include "foeed.h"
@@ -570,6 +571,208 @@ const char *foeed_last_error(void) { return g_err; }
 const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solve: many images, one launch per FSI step over all their tiles.
+
+namespace {
+
+struct BatchPlan {
+    std::vector<Layout> lay;
+    std::vector<size_t> off;  // workspace offset of each image's region
+    size_t inst_off, tiles_off, total;
+    int ntiles;
+};
+
+foeed_status batch_plan(const foeed_instance *inst, int count, foeed_dtype d, BatchPlan *bp)
+{
+    if (!inst || count < 1) return fail(FOEED_ERR_ARG, "need at least one image");
+    bp->lay.resize(count);
+    bp->off.resize(count);
+    size_t off = 0;
+    bp->inst_off = off;
+    off += align_up(sizeof(BatchInst) * (size_t)count, kAlign);
+    long long ntiles = 0;
+    for (int i = 0; i < count; ++i) {
+        foeed_status st = check_image(inst[i].w, inst[i].h, inst[i].pitch, d);
+        if (st) {
+            char msg[sizeof(g_err)];
+            std::snprintf(msg, sizeof(msg), "%s", g_err);
+            return fail(st, "image %d: %s", i, msg);
+        }
+        ntiles += (long long)((inst[i].w + 63) / 64) * ((inst[i].h + 31) / 32);
+    }
+    if (ntiles > (1LL << 30)) return fail(FOEED_ERR_ARG, "too many tiles");
+    bp->ntiles = (int)ntiles;
+    bp->tiles_off = off;
+    off += align_up(sizeof(int2) * (size_t)ntiles, kAlign);
+    for (int i = 0; i < count; ++i) {
+        bp->lay[i] = layout(inst[i].w, inst[i].h, d);
+        bp->off[i] = off;
+        off += bp->lay[i].total;
+    }
+    bp->total = off;
+    return FOEED_OK;
+}
+
+}  // namespace
+
+extern "C" size_t foeed_batch_workspace_bytes(const foeed_instance *inst, int count, foeed_dtype dtype)
+{
+    BatchPlan bp;
+    if (batch_plan(inst, count, dtype, &bp) != FOEED_OK) return 0;
+    return bp.total;
+}
+
+extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
+                                            const foeed_params *params, void *workspace, size_t workspace_bytes,
+                                            void *stream, foeed_report *reports)
+{
+    foeed_status st;
+    if ((st = check_params(params, true))) return st;
+    const foeed_params &p = *params;
+    if (dtype != FOEED_F32 && dtype != FOEED_F32_F64U)
+        return fail(FOEED_ERR_ARG, "the batched solver runs FOEED_F32 or FOEED_F32_F64U");
+    if (!fast_params(false, p))
+        return fail(FOEED_ERR_ARG, "the batched solver needs the Charbonnier diffusivity and mu3 = sqrt(mu1)");
+    if (p.cycle_len < 2) return fail(FOEED_ERR_ARG, "the batched solver needs cycle_len >= 2");
+    BatchPlan bp;
+    if ((st = batch_plan(inst, count, dtype, &bp))) return st;
+    for (int i = 0; i < count; ++i) {
+        if (!inst[i].f || !inst[i].mask || !inst[i].u_inout) return fail(FOEED_ERR_ARG, "image %d: NULL pointer", i);
+        if (!(inst[i].lambda > 0.0) || !std::isfinite(inst[i].lambda))
+            return fail(FOEED_ERR_ARG, "image %d: lambda must be > 0", i);
+    }
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign)
+        return fail(FOEED_ERR_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < bp.total)
+        return fail(FOEED_ERR_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, bp.total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    const bool f64u = dtype == FOEED_F32_F64U;
+    const int R = gauss_radius(p.sigma);
+    const double tau = default_tau(false, p.tau);
+
+    // device tables: one entry per image, one (image, tile) pair per CTA
+    std::vector<BatchInst> hi(count);
+    std::vector<int2> ht((size_t)bp.ntiles);
+    size_t t = 0;
+    for (int i = 0; i < count; ++i) {
+        const Layout &L = bp.lay[i];
+        char *b = ws + bp.off[i];
+        BatchInst &I = hi[i];
+        I.C = reinterpret_cast<float *>(b + L.bufC);
+        I.A = reinterpret_cast<float *>(b + L.bufA);
+        I.B = reinterpret_cast<float *>(b + L.bufB);
+        I.mask = reinterpret_cast<const uint8_t *>(b + L.mask);
+        I.w = inst[i].w;
+        I.h = inst[i].h;
+        I.pitch = L.P;
+        I.c4 = float(0.25 / (inst[i].lambda * inst[i].lambda));
+        I.ntx = (inst[i].w + 63) / 64;
+        I.nty = (inst[i].h + 31) / 32;
+        I.ctl = reinterpret_cast<Ctl *>(b + L.ctl);
+        I.partials = reinterpret_cast<double *>(b + L.partials);
+        for (int k = 0; k < I.ntx * I.nty; ++k) ht[t++] = make_int2(i, k);
+    }
+    CK(cudaMemcpyAsync(ws + bp.inst_off, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws + bp.tiles_off, ht.data(), sizeof(int2) * ht.size(), cudaMemcpyHostToDevice, s));
+
+    // per-image set-up: control block, internal mask, initial image
+    Ctl h0;
+    std::memset(&h0, 0, sizeof(h0));
+    h0.tol = p.tol;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaEventRecord(ev0, s));
+    for (int i = 0; i < count; ++i) {
+        CK(cudaMemcpyAsync(hi[i].ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        CK(launch_prep<float>(inst[i].f, inst[i].mask, inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch,
+                              bp.lay[i], ws + bp.off[i], p.init_mode, s));
+    }
+
+    // one FSI cycle = n launches over the work list, captured once
+    StepCall c{};
+    c.w = 1; c.h = 1; c.pitch = 4;
+    c.tau = tau;
+    StepArgs<float> a = make_args<float>(c, p);
+    CK(batch_step_fast_foeed_f32(nullptr, nullptr, 0, R, f64u, s));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaStream_t cs = g_capture_stream[dev & 63];
+    if (!cs) {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        g_capture_stream[dev & 63] = cs;
+    }
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    const int n = p.cycle_len;
+    for (int k = 0; k < n && err == cudaSuccess; ++k) {
+        BatchArgs b;
+        b.inst = reinterpret_cast<const BatchInst *>(ws + bp.inst_off);
+        b.tiles = reinterpret_cast<const int2 *>(ws + bp.tiles_off);
+        b.role = k == 0 ? kRoleFirst : k == 1 ? kRoleSecond : (k % 2 == 0 ? kRoleEven : kRoleOdd);
+        b.last = k == n - 1;
+        a.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
+        a.alpha_t = float(a.alpha);
+        a.residual = b.last;
+        a.pdl = k > 0;
+        err = batch_step_fast_foeed_f32(&a, &b, bp.ntiles, R, f64u, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(FOEED_ERR_CUDA, "capturing the batched cycle: %s",
+                    cudaGetErrorString(err != cudaSuccess ? err : e2));
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) return fail(FOEED_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+
+    const int every = p.check_every > 0 ? p.check_every : 8;
+    std::vector<Ctl> hc(count);
+    foeed_status result = FOEED_OK;
+    for (int m = 0; m < p.max_cycles && err == cudaSuccess; ++m) {
+        err = cudaGraphLaunch(exec, s);
+        if (err == cudaSuccess && p.tol > 0.0 && ((m + 1) % every == 0) && m + 1 < p.max_cycles) {
+            for (int i = 0; i < count && err == cudaSuccess; ++i)
+                err = cudaMemcpyAsync(&hc[i], hi[i].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+            bool all = true;
+            for (int i = 0; i < count; ++i) all = all && hc[i].done;
+            if (all) break;
+        }
+    }
+    for (int i = 0; i < count && err == cudaSuccess; ++i)
+        err = launch_copy_out<float>(bp.lay[i], ws + bp.off[i], inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch, s);
+    if (err == cudaSuccess) err = cudaEventRecord(ev1, s);
+    for (int i = 0; i < count && err == cudaSuccess; ++i)
+        err = cudaMemcpyAsync(&hc[i], hi[i].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    if (err != cudaSuccess) return fail(FOEED_ERR_CUDA, "batched solve: %s", cudaGetErrorString(err));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    for (int i = 0; i < count; ++i) {
+        if (reports) {
+            reports[i].cycles_run = hc[i].cycles;
+            reports[i].last_rel_change = hc[i].last_rel;
+            reports[i].converged = (p.tol > 0.0 && hc[i].done && !hc[i].diverged) ? 1 : 0;
+            reports[i].ms = ms;
+        }
+        if (result == FOEED_OK && hc[i].diverged)
+            result = fail(FOEED_ERR_DIVERGED, "image %d: cycle %d produced a non-finite change", i, hc[i].cycles);
+        else if (result == FOEED_OK && p.tol > 0.0 && !hc[i].done)
+            result = fail(FOEED_ERR_NOT_CONVERGED, "image %d did not reach tol %.3e", i, p.tol);
+    }
+    if (result == FOEED_OK) g_err[0] = 0;
+    return result;
+}
 
 // ---------------------------------------------------------------------------
 // Solver entry point that allocates nothing.

@@ -24,4 +24,9 @@ cudaError_t step_eed_f64(const StepArgs<double> *a, int R, cudaStream_t s);
 cudaError_t step_fast_foeed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
 cudaError_t step_fast_eed_f32(const StepArgs<float> *a, int R, bool f64_update, cudaStream_t s);
 
+// One FOEED step over the tiles of many images (batched solve); a == nullptr
+// only prepares the kernel.
+cudaError_t batch_step_fast_foeed_f32(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R,
+                                      bool f64_update, cudaStream_t s);
+
 }  // namespace foeed

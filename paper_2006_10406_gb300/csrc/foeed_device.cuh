@@ -86,6 +86,30 @@ cudaError_t launch_step_kernel(Kern kern, dim3 grid, int threads, size_t smem, c
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+// One image of a batched solve (entry of a device table).
+struct BatchInst {
+    float *C, *A, *B;     // the image's cycle buffers (internal pitch)
+    const uint8_t *mask;  // internal 0/1 mask
+    int w, h;
+    long pitch;
+    float c4;             // 1/(4 lambda^2) of this image
+    int ntx, nty;         // its 64 x 32 tile grid
+    Ctl *ctl;             // its control block (cycle residual, stop flag)
+    double *partials;     // its per-tile residual partials
+};
+
+// Buffer roles of one step of a cycle of length n >= 2 (the rotation of the
+// single-image solver): step 0 (C,C)->A, step 1 (C,A)->B, even k >= 2
+// (A,B)->A, odd k >= 3 (B,A)->B; the last step writes C instead.
+enum BatchRole { kRoleFirst = 0, kRoleSecond = 1, kRoleEven = 2, kRoleOdd = 3 };
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const int2 *tiles;  // per CTA: (image, tile index within the image)
+    int role;
+    int last;           // last step of the cycle (writes C, accumulates the residual)
+};
+
 __device__ __forceinline__ int mirror_idx(int i, int n)
 {
     if ((unsigned)i < (unsigned)n) return i;

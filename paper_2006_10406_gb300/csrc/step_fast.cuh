@@ -55,34 +55,39 @@ struct FastTile {
     static constexpr size_t SMEM = sizeof(float) * ELEMS;
 };
 
+// The image one tile belongs to: its buffers for this step and its geometry.
+struct TileImg {
+    const float *uprev, *ucur;
+    float *unext;
+    const uint8_t *mask;  // may be null
+    const float *c0;      // cycle start (residual steps)
+    int w, h;
+    long pitch;
+    float c4;             // 1/(4 lambda^2)
+};
+
+// One 64 x 32 tile of one FSI step (stages A..E) of image im; p supplies the
+// Gaussian taps, alpha, tau and whether this step accumulates the cycle
+// residual (added to rnum/rden).
 template <int R, bool EED, typename U>
-__global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
+__device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileImg &im, const int x0, const int y0,
+                                          float *sm, double &rnum, double &rden)
 {
     using G = FastTile<R, EED>;
-    extern __shared__ __align__(16) float sm[];
     float *su = sm;
     float *sx = su + G::SU_W * G::SU_H;
     float *st = sx;  // aliases sx: written in stage D, after the last read of sx in stage C
     float *ss = sx + G::SXT;
-    __shared__ double red[64];
-
-    // Programmatic dependent launch: wait until the previous step's grid has
-    // completed and its writes are visible (a no-op for an ordinary launch),
-    // then let the next step's CTAs be scheduled as SM slots free up.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (p.check_done && p.ctl->done) return;
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const U alpha = sizeof(U) == sizeof(float) ? U(p.alpha_t) : U(p.alpha);
     const U tau = sizeof(U) == sizeof(float) ? U(p.tau_t) : U(p.tau);
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * G::TH;
-    const int w = p.w, h = p.h;
-    const long pitch = p.pitch;
+    const int w = im.w, h = im.h;
+    const long pitch = im.pitch;
 
     // ---- A: u window, copied global -> shared asynchronously (cp.async) ----
     {
-        const float *__restrict__ uc = p.ucur;
+        const float *__restrict__ uc = im.ucur;
         const bool xin = (x0 - 8 >= 0) && (x0 + 76 <= w);
         const bool yin = (y0 - G::HL >= 0) && (y0 + G::TH + G::HL <= h);
         constexpr int NQ = G::SU_W / 4;  // 21 float4 per row
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
     // ---- D: on tile+-1 (T row r <-> tile row r-1, T col 4q+k <-> tile col 4q+k-1) ----
     constexpr int PL = G::ST_W * G::ST_H;
     {
-        const float c4 = p.c4;
+        const float c4 = im.c4;
         constexpr int NQ = G::ST_W / 4;  // 17
         for (int i = tid; i < G::ST_H * NQ; i += 256) {
             int q = i / G::ST_H, r = i - q * G::ST_H;
@@ -271,14 +276,14 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
         if (gy < h && gx < w) {
             const long gi = (long)gy * pitch + gx;
             if (gx + 3 < w) {
-                pre_up[e] = __ldg(reinterpret_cast<const float4 *>(p.uprev + gi));
-                if (p.mask) pre_mk[e] = __ldg(reinterpret_cast<const unsigned int *>(p.mask + gi));
+                pre_up[e] = __ldg(reinterpret_cast<const float4 *>(im.uprev + gi));
+                if (im.mask) pre_mk[e] = __ldg(reinterpret_cast<const unsigned int *>(im.mask + gi));
             } else {
                 float *pu = reinterpret_cast<float *>(&pre_up[e]);
                 for (int k = 0; k < 4; ++k)
                     if (gx + k < w) {
-                        pu[k] = p.uprev[gi + k];
-                        if (p.mask) pre_mk[e] |= uint32_t(p.mask[gi + k] != 0) << (8 * k);
+                        pu[k] = im.uprev[gi + k];
+                        if (im.mask) pre_mk[e] |= uint32_t(im.mask[gi + k] != 0) << (8 * k);
                     }
             }
         }
@@ -286,7 +291,6 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
     __syncthreads();
 
     // ---- E: output rows tile+r, columns tile+4q .. 4q+3 (T index (r+1, 4q+1+k)) ----
-    double rnum = 0.0, rden = 0.0;
     {
         constexpr int NQ = NQE;
 #pragma unroll
@@ -364,11 +368,11 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
             float c0v[4] = {0.f, 0.f, 0.f, 0.f};
             if (p.residual) {
                 if (full) {
-                    float4 c = *reinterpret_cast<const float4 *>(p.c0 + gi);
+                    float4 c = *reinterpret_cast<const float4 *>(im.c0 + gi);
                     c0v[0] = c.x; c0v[1] = c.y; c0v[2] = c.z; c0v[3] = c.w;
                 } else {
                     for (int k = 0; k < 4; ++k)
-                        if (gx + k < w) c0v[k] = p.c0[gi + k];
+                        if (gx + k < w) c0v[k] = im.c0[gi + k];
                 }
             }
             float un[4];
@@ -392,29 +396,107 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
                     }
             }
             if (full) {
-                *reinterpret_cast<float4 *>(p.unext + gi) = make_float4(un[0], un[1], un[2], un[3]);
+                *reinterpret_cast<float4 *>(im.unext + gi) = make_float4(un[0], un[1], un[2], un[3]);
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if (gx + k < w) p.unext[gi + k] = un[k];
+                    if (gx + k < w) im.unext[gi + k] = un[k];
             }
         }
     }
 
-    if (p.residual) {
-        const int nblocks = gridDim.x * gridDim.y;
-        const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-        if (grid_sum2_last(rnum, rden, p.partials, &p.ctl->ticket, nblocks, bid, red)) {
-            Ctl *ctl = p.ctl;
-            double rel = rden > 0.0 ? sqrt(rnum) / sqrt(rden) : sqrt(rnum);
-            ctl->last_num = rnum;
-            ctl->last_den = rden;
-            ctl->last_rel = rel;
-            ctl->cycles += 1;
-            if (!isfinite(rel)) { ctl->diverged = 1; ctl->done = 1; }
-            else if (ctl->tol > 0.0 && rel < ctl->tol) ctl->done = 1;
-        }
+}
+
+// Cycle residual of one image: the last of its nblocks tiles to finish sums
+// the per-tile partials in tile order and updates its control block.
+__device__ __forceinline__ void finish_cycle_residual(double rnum, double rden, Ctl *ctl, double *partials,
+                                                      int nblocks, int bid, double *red)
+{
+    if (grid_sum2_last(rnum, rden, partials, &ctl->ticket, nblocks, bid, red)) {
+        double rel = rden > 0.0 ? sqrt(rnum) / sqrt(rden) : sqrt(rnum);
+        ctl->last_num = rnum;
+        ctl->last_den = rden;
+        ctl->last_rel = rel;
+        ctl->cycles += 1;
+        if (!isfinite(rel)) { ctl->diverged = 1; ctl->done = 1; }
+        else if (ctl->tol > 0.0 && rel < ctl->tol) ctl->done = 1;
     }
+}
+
+// One FSI step over one image, one CTA per 64 x 32 tile.
+template <int R, bool EED, typename U>
+__global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[64];
+    // Programmatic dependent launch: wait until the previous step's grid has
+    // completed and its writes are visible (a no-op for an ordinary launch),
+    // then let the next step's CTAs be scheduled as SM slots free up.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (p.check_done && p.ctl->done) return;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const TileImg im{p.uprev, p.ucur, p.unext, p.mask, p.c0, p.w, p.h, p.pitch, p.c4};
+    double rnum = 0.0, rden = 0.0;
+    fast_tile<R, EED, U>(p, im, blockIdx.x * FastTile<R, EED>::TW, blockIdx.y * FastTile<R, EED>::TH, sm, rnum, rden);
+    if (p.residual)
+        finish_cycle_residual(rnum, rden, p.ctl, p.partials, gridDim.x * gridDim.y,
+                              blockIdx.y * gridDim.x + blockIdx.x, red);
+}
+
+// ---------------------------------------------------------------------------
+// Batched FOEED: one launch per FSI step over the tiles of many images.
+
+template <int R, typename U>
+__global__ void __launch_bounds__(256) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[64];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int2 tl = b.tiles[blockIdx.x];
+    const BatchInst I = b.inst[tl.x];
+    if (I.ctl->done) return;  // this image has converged (or diverged)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    TileImg im;
+    switch (b.role) {
+    case kRoleFirst: im.uprev = I.C; im.ucur = I.C; im.unext = I.A; break;
+    case kRoleSecond: im.uprev = I.C; im.ucur = I.A; im.unext = I.B; break;
+    case kRoleEven: im.uprev = I.A; im.ucur = I.B; im.unext = I.A; break;
+    default: im.uprev = I.B; im.ucur = I.A; im.unext = I.B; break;
+    }
+    if (b.last) im.unext = I.C;
+    im.mask = I.mask;
+    im.c0 = I.C;
+    im.w = I.w;
+    im.h = I.h;
+    im.pitch = I.pitch;
+    im.c4 = I.c4;
+    const int ty = tl.y / I.ntx, tx = tl.y - ty * I.ntx;
+    double rnum = 0.0, rden = 0.0;
+    fast_tile<R, false, U>(p, im, tx * FastTile<R, false>::TW, ty * FastTile<R, false>::TH, sm, rnum, rden);
+    if (b.last) finish_cycle_residual(rnum, rden, I.ctl, I.partials, I.ntx * I.nty, tl.y, red);
+}
+
+template <int R, typename U>
+cudaError_t launch_fsi_batch_step_fast(const StepArgs<float> *ap, const BatchArgs *bp, int ntiles, cudaStream_t s)
+{
+    using G = FastTile<R, false>;
+    auto kern = fsi_batch_step_fast<R, U>;
+    if (!ap) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (!ap->pdl) {
+        kern<<<ntiles, 256, G::SMEM, s>>>(*ap, *bp);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntiles);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, *ap, *bp);
 }
 
 template <int R, bool EED, typename U>

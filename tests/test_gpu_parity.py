@@ -325,3 +325,58 @@ def test_generic_f32_variants(g_kind, mu3):
     out = torch.empty_like(b)
     fg.foeed_step(b, b, out, m, 2.0 / 3.0, 0.05, 1.0, tau=0.05, diffusivity=g_kind, mu3_mode=mu3)
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=2e-5)
+
+
+# --------------------------------------------------------------------------
+# batched solve: many images of uneven sizes in one launch per FSI step;
+# each result must equal the single-image solve bit for bit
+
+def _batch_case(seed=0, sizes=((64, 64), (96, 130), (33, 200), (128, 64), (7, 9), (250, 41))):
+    imgs, masks, lams = [], [], []
+    for i, (h, w) in enumerate(sizes):
+        img, mask, _ = synth.workload(2, h=h, w=w, instance=seed + i)
+        imgs.append(torch.from_numpy(img.astype(np.float32)).to(DEV))
+        masks.append(torch.from_numpy(mask).to(DEV))
+        lams.append(0.01 + 0.015 * i)
+    return imgs, masks, lams
+
+
+@pytest.mark.parametrize("n", [2, 3, 25])
+@pytest.mark.parametrize("dtype", ["f32", "f32_f64u"])
+def test_batch_equals_single_image_solves(n, dtype):
+    imgs, masks, lams = _batch_case()
+    outs, reps = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, 4, dtype=dtype)
+    for f, m, lam, u, r in zip(imgs, masks, lams, outs, reps):
+        ref, rr = fg.foeed_inpaint(f, m, lam, 1.0, n, 4, dtype=dtype)
+        assert r.cycles_run == rr.cycles_run == 4
+        assert torch.equal(u, ref), float((u - ref).abs().max())
+        assert r.last_rel_change == rr.last_rel_change
+
+
+def test_batch_matches_oracle_and_keeps_known_pixels():
+    imgs, masks, lams = _batch_case(seed=50, sizes=((40, 56), (23, 31)))
+    outs, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 10, 3)
+    for f, m, lam, u in zip(imgs, masks, lams, outs):
+        f64 = f.double().cpu().numpy()
+        ref, _, _ = O.inpaint(0, f64, m.cpu().numpy(), 1.0, lam, 10, 3)
+        got = u.double().cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 2e-4
+        k = m.cpu().numpy() != 0
+        np.testing.assert_array_equal(u.cpu().numpy()[k], f.cpu().numpy()[k])
+
+
+def test_batch_tolerance_stops_each_image_like_its_single_solve():
+    imgs, masks, lams = _batch_case(seed=70, sizes=((48, 40), (32, 96), (70, 70)))
+    outs, reps = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 10, 2000, tol=1e-4, check_every=3)
+    for f, m, lam, u, r in zip(imgs, masks, lams, outs, reps):
+        ref, rr = fg.foeed_inpaint(f, m, lam, 1.0, 10, 2000, tol=1e-4, check_every=3)
+        assert r.converged and rr.converged and r.cycles_run == rr.cycles_run
+        assert torch.equal(u, ref)
+
+
+def test_batch_rejects_unsupported_configurations():
+    imgs, masks, lams = _batch_case(sizes=((16, 16),))
+    with pytest.raises(fg.FoeedError):
+        fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 1, 2)
+    with pytest.raises(fg.FoeedError):
+        fg.foeed_inpaint_batch(imgs, masks, [-1.0], 1.0, 4, 2)
