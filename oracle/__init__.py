@@ -59,6 +59,10 @@ def lib():
         L.orc_inpaint.argtypes = [i, _D, _U8, _D, i, i, d, d, d, i, i, d, i, i, i, _D]
         L.orc_inpaint.restype = i
         L.orc_errors.argtypes = [_D, _D, C.c_long, _D]
+        L.orc_foeed_tensor_grad.argtypes = [d, d, d, i, _D]
+        L.orc_foeed_vjp_F.argtypes = [_D, _D, i, i, d, d, i, _D]
+        L.orc_inpaint_vjp.argtypes = [_D, _U8, _D, _D, vp, i, i, d, d, d, i, i, i]
+        L.orc_inpaint_vjp.restype = i
         _lib = L
     return _lib
 
@@ -205,3 +209,33 @@ def errors(u, v):
     out = np.zeros(2)
     lib().orc_errors(u.reshape(-1), v.reshape(-1), u.size, out)
     return float(out[0]), float(out[1])
+
+
+def foeed_tensor_grad(gx, gy, lam, mu3_mode=MU3_GEOMETRIC):
+    """d d_ijkl / d g_m of the Charbonnier FOEED tensor, shape [2 (m), 2, 2, 2, 2]."""
+    dd = np.zeros(32)
+    lib().orc_foeed_tensor_grad(float(gx), float(gy), float(lam), int(mu3_mode), dd)
+    return dd.reshape(2, 2, 2, 2, 2)
+
+
+def foeed_vjp_F(x, v, sigma, lam, mu3_mode=MU3_GEOMETRIC):
+    """J_F(x)^T v for the FOEED operator F(x) = P(x) x (Charbonnier)."""
+    x = _f64(x); v = _f64(v); h, w = x.shape
+    out = np.empty_like(x)
+    lib().orc_foeed_vjp_F(x, v, w, h, float(sigma), float(lam), int(mu3_mode), out)
+    return out
+
+
+def inpaint_vjp(f, mask, grad_u, sigma, lam, cycle_len, cycles, tau=0.0, mu3_mode=MU3_GEOMETRIC):
+    """dL/df on the known pixels for L with dL/du_final = grad_u, through the whole
+    FOEED FSI solve (init from the mean of f over K, fixed cycles). Returns (grad_f, u_final)."""
+    f = _f64(f); h, w = f.shape
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    gu = _f64(grad_u)
+    gf = np.zeros_like(f)
+    uf = np.zeros_like(f)
+    st = lib().orc_inpaint_vjp(f, mask, gu, gf, uf.ctypes.data, w, h, float(sigma), float(lam), float(tau),
+                               int(cycle_len), int(cycles), int(mu3_mode))
+    if st:
+        raise ValueError("bad arguments")
+    return gf, uf

@@ -475,3 +475,201 @@ void orc_errors(const double *u, const double *v, long n, double out[2])
     out[0] = se / (double)n;
     out[1] = ae / (double)n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint (vector-Jacobian product) of the FOEED inpainting solve, for tonal
+ * optimisation of the stored grey values. The paper has no adjoint; this is
+ * the exact derivative of the discrete solve above (Charbonnier diffusivity),
+ * written out step by step in its plainest form: every transpose is applied
+ * by scattering the forward stencil's weights, and the tensor derivative is
+ * taken from the literal spectral sum d = sum_r mu_r E_r (x) E_r. */
+
+/* d d_ijkl / d g_m for the Charbonnier tensor at gradient g = (gx, gy):
+ * dd[m*16 + ((i*2+j)*2+k)*2+l]. */
+void orc_foeed_tensor_grad(double gx, double gy, double lambda, int mu3_mode, double dd[32])
+{
+    double v1[2], v2[2], dv1[2][2], dv2[2][2]; /* dv1[m][i] = d v1_i / d g_m */
+    eigvec(gx, gy, &v1[0], &v1[1]);
+    v2[0] = -v1[1];
+    v2[1] = v1[0];
+    double rho2 = gx * gx + gy * gy;
+    double rho = sqrt(rho2);
+    for (int m = 0; m < 2; ++m)
+        for (int i = 0; i < 2; ++i)
+            dv1[m][i] = rho > 0.0 ? ((i == m ? 1.0 : 0.0) - v1[i] * v1[m]) / rho : 0.0;
+    for (int m = 0; m < 2; ++m) {
+        dv2[m][0] = -dv1[m][1];
+        dv2[m][1] = dv1[m][0];
+    }
+    double mu1 = orc_diffusivity(0, rho2, lambda);
+    double mu3 = mu3_of(mu3_mode, mu1, 1.0);
+    double g[2] = {gx, gy};
+    double dmu[4][2];
+    for (int m = 0; m < 2; ++m) {
+        /* mu1 = (1 + rho^2/lambda^2)^(-1/2): d mu1 / d g_m = -mu1^3 g_m / lambda^2 */
+        dmu[0][m] = -mu1 * mu1 * mu1 * g[m] / (lambda * lambda);
+        dmu[1][m] = 0.0;
+        dmu[2][m] = mu3_mode == 0 ? dmu[0][m] / (2.0 * mu3) : (mu3_mode == 1 ? dmu[0][m] / 2.0 : 0.0);
+        dmu[3][m] = 0.0;
+    }
+    double mu[4] = {mu1, 1.0, mu3, 0.0};
+    double r2 = 1.0 / sqrt(2.0);
+    double E[4][2][2], dE[2][4][2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            E[0][i][j] = v1[i] * v1[j];
+            E[1][i][j] = v2[i] * v2[j];
+            E[2][i][j] = r2 * (v1[i] * v2[j] + v2[i] * v1[j]);
+            E[3][i][j] = r2 * (v1[i] * v2[j] - v2[i] * v1[j]);
+            for (int m = 0; m < 2; ++m) {
+                dE[m][0][i][j] = dv1[m][i] * v1[j] + v1[i] * dv1[m][j];
+                dE[m][1][i][j] = dv2[m][i] * v2[j] + v2[i] * dv2[m][j];
+                dE[m][2][i][j] = r2 * (dv1[m][i] * v2[j] + v1[i] * dv2[m][j] + dv2[m][i] * v1[j] + v2[i] * dv1[m][j]);
+                dE[m][3][i][j] = r2 * (dv1[m][i] * v2[j] + v1[i] * dv2[m][j] - dv2[m][i] * v1[j] - v2[i] * dv1[m][j]);
+            }
+        }
+    for (int m = 0; m < 2; ++m)
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j)
+                for (int k = 0; k < 2; ++k)
+                    for (int l = 0; l < 2; ++l) {
+                        double s = 0.0;
+                        for (int r = 0; r < 4; ++r)
+                            s += dmu[r][m] * E[r][i][j] * E[r][k][l] +
+                                 mu[r] * (dE[m][r][i][j] * E[r][k][l] + E[r][i][j] * dE[m][r][k][l]);
+                        dd[m * 16 + ((i * 2 + j) * 2 + k) * 2 + l] = s;
+                    }
+}
+
+/* Transpose of the separable mirrored Gaussian, applied by scattering. */
+static void presmooth_T(const double *ubar_s, int w, int h, double sigma, double *ubar)
+{
+    double wts[257];
+    int R = orc_gauss_weights(sigma, wts, 257);
+    size_t n = (size_t)w * h;
+    double *tmp = (double *)calloc(n, sizeof(double));
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x)
+            for (int t = -R; t <= R; ++t) tmp[(size_t)mirror(y + t, h) * w + x] += wts[t + R] * ubar_s[(size_t)y * w + x];
+    memset(ubar, 0, sizeof(double) * n);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x)
+            for (int t = -R; t <= R; ++t) ubar[(size_t)y * w + mirror(x + t, w)] += wts[t + R] * tmp[(size_t)y * w + x];
+    free(tmp);
+}
+
+/* J_F(x)^T v for F(x) = P(x) x (FOEED operator, Charbonnier): the frozen-tensor
+ * part P(x)^T v = P(x) v (P is symmetric), plus the tensor's dependence on x
+ * through the pre-smoothed gradient: q_m = sum_ijkl (H(v))_ij (H(x))_kl
+ * d d_ijkl / d g_m, pulled back through the central-difference gradient and
+ * the Gaussian by their transposes. */
+void orc_foeed_vjp_F(const double *x, const double *v, int w, int h, double sigma, double lambda, int mu3_mode,
+                     double *out)
+{
+    size_t n = (size_t)w * h;
+    double *d = (double *)malloc(sizeof(double) * 16 * n);
+    double *us = (double *)malloc(sizeof(double) * n);
+    double *gx = (double *)malloc(sizeof(double) * n);
+    double *gy = (double *)malloc(sizeof(double) * n);
+    double *Hx[3], *Hv[3];
+    for (int c = 0; c < 3; ++c) {
+        Hx[c] = (double *)malloc(sizeof(double) * n);
+        Hv[c] = (double *)malloc(sizeof(double) * n);
+    }
+    double *r = (double *)calloc(n, sizeof(double));
+    double *z = (double *)malloc(sizeof(double) * n);
+    orc_presmooth(x, w, h, sigma, us);
+    orc_gradient(us, w, h, gx, gy);
+    for (size_t p = 0; p < n; ++p) orc_foeed_tensor(gx[p], gy[p], lambda, 0, mu3_mode, d + p * 16, NULL);
+    orc_apply_P_field(v, d, w, h, out); /* P(x) v */
+    orc_hessian(x, w, h, Hx[0], Hx[1], Hx[2]);
+    orc_hessian(v, w, h, Hv[0], Hv[1], Hv[2]);
+    for (int y = 0; y < h; ++y)
+        for (int xx = 0; xx < w; ++xx) {
+            size_t p = (size_t)y * w + xx;
+            double dd[32];
+            orc_foeed_tensor_grad(gx[p], gy[p], lambda, mu3_mode, dd);
+            double W[2][2] = {{Hv[0][p], Hv[1][p]}, {Hv[1][p], Hv[2][p]}};
+            double H[2][2] = {{Hx[0][p], Hx[1][p]}, {Hx[1][p], Hx[2][p]}};
+            double q[2] = {0.0, 0.0};
+            for (int m = 0; m < 2; ++m)
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j)
+                        for (int k = 0; k < 2; ++k)
+                            for (int l = 0; l < 2; ++l) q[m] += W[i][j] * H[k][l] * dd[m * 16 + ((i * 2 + j) * 2 + k) * 2 + l];
+            /* transpose of gx = (us[x+1] - us[x-1])/2, gy likewise, by scattering */
+            r[(size_t)y * w + mirror(xx + 1, w)] += 0.5 * q[0];
+            r[(size_t)y * w + mirror(xx - 1, w)] -= 0.5 * q[0];
+            r[(size_t)mirror(y + 1, h) * w + xx] += 0.5 * q[1];
+            r[(size_t)mirror(y - 1, h) * w + xx] -= 0.5 * q[1];
+        }
+    presmooth_T(r, w, h, sigma, z);
+    for (size_t p = 0; p < n; ++p) out[p] += z[p];
+    free(d); free(us); free(gx); free(gy);
+    for (int c = 0; c < 3; ++c) { free(Hx[c]); free(Hv[c]); }
+    free(r); free(z);
+}
+
+/* Gradient of a scalar loss L(u_final) with respect to the stored grey values
+ * f on the known set, through the whole FOEED FSI solve (init_mode 0: unknown
+ * pixels start at the mean of f over K; tol = 0, fixed cycles).
+ *   grad_u: dL/du_final;  grad_f: dL/df on K, 0 elsewhere;  u_final optional.
+ * Forward states are all kept (small images). Returns 0, or 1 for bad input.
+ * Reverse recursion for step u^{k+1} = M u^k + (1-M)(a (u^k - tau F(u^k)) + (1-a) p),
+ * p = u^{k-1} (or u^k at the first step of a cycle):
+ *   du^k   += M g + a (1-M) g - a tau J_F(u^k)^T ((1-M) g)
+ *   dp     += (1-a) (1-M) g */
+int orc_inpaint_vjp(const double *f, const uint8_t *mask, const double *grad_u, double *grad_f, double *u_final,
+                    int w, int h, double sigma, double lambda, double tau, int cycle_len, int cycles, int mu3_mode)
+{
+    if (cycle_len < 1 || cycles < 1) return 1;
+    size_t n = (size_t)w * h;
+    long S = (long)cycle_len * cycles;
+    if (tau <= 0.0) tau = 0.05;
+    double *X = (double *)malloc(sizeof(double) * n * (size_t)(S + 1)); /* x_0 .. x_S */
+    double s = 0.0;
+    long cnt = 0;
+    for (size_t p = 0; p < n; ++p)
+        if (mask[p]) { s += f[p]; ++cnt; }
+    double mean = cnt ? s / (double)cnt : 0.0;
+    for (size_t p = 0; p < n; ++p) X[p] = mask[p] ? f[p] : mean;
+    for (long st = 0; st < S; ++st) {
+        int k = (int)(st % cycle_len);
+        const double *cur = X + (size_t)st * n;
+        const double *prev = k == 0 ? cur : X + (size_t)(st - 1) * n;
+        orc_fsi_step(0, prev, cur, mask, w, h, orc_fsi_alpha(k), tau, sigma, lambda, 0, mu3_mode,
+                     X + (size_t)(st + 1) * n);
+    }
+    if (u_final) memcpy(u_final, X + (size_t)S * n, sizeof(double) * n);
+    double *g = (double *)malloc(sizeof(double) * n);    /* dL/dx_{s+1}, complete */
+    double *pend = (double *)calloc(n, sizeof(double));  /* pending dL/dx_s from step s+1 */
+    double *vv = (double *)malloc(sizeof(double) * n);
+    double *jt = (double *)malloc(sizeof(double) * n);
+    memcpy(g, grad_u, sizeof(double) * n);
+    for (long st = S - 1; st >= 0; --st) {
+        int k = (int)(st % cycle_len);
+        double a = orc_fsi_alpha(k);
+        const double *cur = X + (size_t)st * n;
+        for (size_t p = 0; p < n; ++p) vv[p] = mask[p] ? 0.0 : g[p];
+        orc_foeed_vjp_F(cur, vv, w, h, sigma, lambda, mu3_mode, jt);
+        for (size_t p = 0; p < n; ++p) {
+            double m = mask[p] ? 1.0 : 0.0;
+            double dcur = m * g[p] + a * vv[p] - a * tau * jt[p];
+            double dprev = (1.0 - a) * vv[p];
+            if (k == 0) {
+                g[p] = pend[p] + dcur + dprev;
+                pend[p] = 0.0;
+            } else {
+                g[p] = pend[p] + dcur;
+                pend[p] = dprev;
+            }
+        }
+    }
+    /* x_0 = M f + (1 - M) mean(f_K) */
+    double su = 0.0;
+    for (size_t p = 0; p < n; ++p)
+        if (!mask[p]) su += g[p];
+    for (size_t p = 0; p < n; ++p) grad_f[p] = mask[p] ? g[p] + (cnt ? su / (double)cnt : 0.0) : 0.0;
+    free(X); free(g); free(pend); free(vv); free(jt);
+    return 0;
+}
