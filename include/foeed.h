@@ -162,6 +162,29 @@ foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dt
                                  const foeed_params *params, void *workspace, size_t workspace_bytes,
                                  void *stream, foeed_report *reports);
 
+/* Workspace bytes foeed_inpaint_vjp needs (checkpoint every `checkpoint_every` steps). */
+size_t foeed_vjp_workspace_bytes(int w, int h, foeed_dtype dtype, const foeed_params *params,
+                                 int checkpoint_every);
+
+/*
+ * Gradient of a scalar loss of the FOEED reconstruction with respect to the
+ * stored grey values (tonal optimisation). The paper has no adjoint; this is
+ * the exact derivative of the discrete solve of foeed_inpaint: the forward
+ * FSI solve is re-run with a checkpoint of (u^k, u^{k-1}) every
+ * checkpoint_every steps, then each segment is recomputed from its checkpoint
+ * and traversed backwards with the adjoint step kernels.
+ *   grad_u  [h x pitch] dL/du_final (device)
+ *   grad_f  [h x pitch] out: dL/df on the known pixels, 0 elsewhere; includes
+ *           the path through the mean initialisation of the unknown pixels
+ *   u_out   [h x pitch] out (may be NULL): the reconstruction u_final
+ * Requirements: FOEED_F32 or FOEED_F64, Charbonnier diffusivity, mu3 =
+ * sqrt(mu1), init_mode 0, tol 0 (a fixed number of cycles). Synchronises
+ * `stream` at the end.
+ */
+foeed_status foeed_inpaint_vjp(const void *f, const uint8_t *mask, const void *grad_u, void *grad_f, void *u_out,
+                               int w, int h, long pitch, foeed_dtype dtype, const foeed_params *params,
+                               int checkpoint_every, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Bytes of workspace foeed_errors needs for a w x h image. */
 size_t foeed_errors_workspace_bytes(int w, int h);
 

@@ -22,8 +22,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "foeed_step", "eed_step", "foeed_errors",
-           "workspace_bytes",
+__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "foeed_inpaint_vjp", "foeed_inpaint_diff",
+           "foeed_step", "eed_step", "foeed_errors", "workspace_bytes",
            "Report", "FoeedError", "lib", "F32", "F64", "F32_F64U", "STATUS"]
 
 F32, F64, F32_F64U = 0, 1, 2
@@ -91,6 +91,10 @@ def lib():
         L.foeed_inpaint_batch.argtypes = [C.POINTER(_Instance), i, i, C.POINTER(_Params), vp, sz, vp,
                                           C.POINTER(_Report)]
         L.foeed_inpaint_batch.restype = i
+        L.foeed_vjp_workspace_bytes.argtypes = [i, i, i, C.POINTER(_Params), i]
+        L.foeed_vjp_workspace_bytes.restype = sz
+        L.foeed_inpaint_vjp.argtypes = [vp, vp, vp, vp, vp, i, i, C.c_long, i, C.POINTER(_Params), i, vp, sz, vp]
+        L.foeed_inpaint_vjp.restype = i
         L.foeed_errors_workspace_bytes.argtypes = [i, i]
         L.foeed_errors_workspace_bytes.restype = sz
         L.foeed_errors.argtypes = [vp, vp, i, i, C.c_long, i, vp, sz, vp, C.POINTER(C.c_double)]
@@ -263,6 +267,75 @@ def foeed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, ta
         _check(st)
     reports = [Report(st, r.cycles_run, r.last_rel_change, bool(r.converged), r.ms) for r in reps]
     return outs, reports
+
+
+def foeed_inpaint_vjp(f, mask, grad_u, lam, sigma, cycle_len, max_cycles, tau=0.0, checkpoint_every=16,
+                      stream=None, workspace=None):
+    """Gradient of a loss of the FOEED reconstruction with respect to the stored grey
+    values: grad_f = (d u_final / d f)^T grad_u on the known pixels (0 elsewhere),
+    through the whole FSI solve (mean initialisation, fixed cycles), recomputed from
+    checkpoints every `checkpoint_every` steps. f, mask, grad_u: 2-D CUDA tensors
+    (float32 or float64, one row pitch). Returns (grad_f, u_final)."""
+    torch = _torch()
+    for t in (f, grad_u):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2 and t.stride(1) == 1):
+            raise FoeedError(1, "f and grad_u must be 2-D CUDA tensors with unit column stride")
+    h, w = f.shape
+    pitch = f.stride(0)
+    if grad_u.stride(0) != pitch or grad_u.dtype != f.dtype:
+        grad_u = _pitched_like(grad_u.to(f.dtype), pitch)
+    if not (mask.is_cuda and mask.dtype == torch.uint8 and mask.stride(0) == pitch and mask.stride(1) == 1):
+        mask = _pitched_like(mask.to(f.device, torch.uint8), pitch)
+    code = F64 if f.dtype == torch.float64 else F32
+    p = _params(lam, sigma, tau, cycle_len, max_cycles, 0.0, 0, 0, 0, 8)
+    nbytes = int(lib().foeed_vjp_workspace_bytes(w, h, code, C.byref(p), int(checkpoint_every)))
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=f.device)
+    gf = torch.empty_strided((h, w), (pitch, 1), dtype=f.dtype, device=f.device)
+    uf = torch.empty_strided((h, w), (pitch, 1), dtype=f.dtype, device=f.device)
+    with torch.cuda.device(f.device):
+        _check(lib().foeed_inpaint_vjp(C.c_void_p(f.data_ptr()), C.c_void_p(mask.data_ptr()),
+                                       C.c_void_p(grad_u.data_ptr()), C.c_void_p(gf.data_ptr()),
+                                       C.c_void_p(uf.data_ptr()), w, h, pitch, code, C.byref(p),
+                                       int(checkpoint_every), C.c_void_p(workspace.data_ptr()),
+                                       workspace.numel(), _stream_ptr(stream)))
+    return gf, uf
+
+
+def _autograd_function():
+    import torch
+
+    class FoeedInpaint(torch.autograd.Function):
+        """u = FOEED inpainting of f on the mask; backward through the hand-written adjoint."""
+
+        @staticmethod
+        def forward(ctx, f, mask, lam, sigma, cycle_len, max_cycles, tau, checkpoint_every):
+            u, _ = foeed_inpaint(f.detach(), mask, lam, sigma, cycle_len, max_cycles, tau=tau)
+            ctx.save_for_backward(f.detach(), mask)
+            ctx.cfg = (lam, sigma, cycle_len, max_cycles, tau, checkpoint_every)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            f, mask = ctx.saved_tensors
+            lam, sigma, n, cycles, tau, K = ctx.cfg
+            gf, _ = foeed_inpaint_vjp(f, mask, grad_u.contiguous(), lam, sigma, n, cycles, tau=tau,
+                                      checkpoint_every=K)
+            return gf, None, None, None, None, None, None, None
+
+    return FoeedInpaint
+
+
+_FoeedInpaint = None
+
+
+def foeed_inpaint_diff(f, mask, lam, sigma, cycle_len, max_cycles, tau=0.0, checkpoint_every=16):
+    """Differentiable FOEED inpainting (torch.autograd): the gradient of any loss of
+    the result flows back to f through foeed_inpaint_vjp."""
+    global _FoeedInpaint
+    if _FoeedInpaint is None:
+        _FoeedInpaint = _autograd_function()
+    return _FoeedInpaint.apply(f, mask, lam, sigma, cycle_len, max_cycles, tau, checkpoint_every)
 
 
 def _step(method, u_prev, u_cur, u_next, mask, alpha, lam, sigma, tau=0.0, diffusivity=0, mu3_mode=0,

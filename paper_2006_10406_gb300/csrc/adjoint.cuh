@@ -1,0 +1,242 @@
+// Backward (adjoint) kernels of one masked FOEED FSI step, for the gradient of
+// a loss of the reconstruction with respect to the stored grey values.
+//
+// Step: u^{k+1} = M u^k + (1-M)(a (u^k - tau F(u^k)) + (1-a) p),  F(x) = P(x) x,
+// p = u^{k-1} (u^k at the first step of a cycle). Given g = dL/du^{k+1}:
+//   v = (1-M) g
+//   J_F(x)^T v = P(x) v + G D^T q,   q = d/d(grad u_sigma) of  H(v) : D(grad u_sigma) : H(x)
+//   dL/du^k += M g + a v - a tau J_F(x)^T v,   dL/dp += (1-a) v
+// P is symmetric (outer operator = transpose of the inner one), so its
+// transpose is P itself; G (mirrored Gaussian) is symmetric; D^T = -D_odd
+// (central difference with odd ghosts).
+//
+// B1 computes P(x) v and q on a tile (the forward stages on x, plus the
+// Hessian of v); B2 applies -D_odd to q, the Gaussian, and the recursion.
+#pragma once
+
+#include "foeed_device.cuh"
+
+namespace foeed {
+
+template <typename T>
+struct AdjArgs {
+    const T *x;          // state u^k (internal pitch)
+    const T *g;          // dL/du^{k+1}
+    const uint8_t *mask; // internal 0/1 mask
+    T *pv;               // out (B1): P(x) v
+    T *qx, *qy;          // out (B1) / in (B2)
+    T *gout;             // out (B2): dL/du^k (may alias g)
+    T *pend;             // in/out (B2): pending dL/du^k from the next step's u^{k-1} use
+    int w, h;
+    long pitch;
+    T alpha, tau;
+    T l2;                // lambda^2
+    T wts[2 * kRMax + 1];
+    int first_of_cycle;  // 1: this step's p is u^k itself
+};
+
+constexpr int kAdjTW = 32, kAdjTH = 16;
+
+// B1: P(x) v and q at every pixel of a 32 x 16 tile.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
+{
+    constexpr int TW = kAdjTW, TH = kAdjTH;
+    constexpr int HL = R + 2;
+    constexpr int XW = TW + 2 * HL, XH = TH + 2 * HL;  // x window
+    constexpr int VW = TW + 4, VH = TH + 4;            // v window (tile +- 2)
+    constexpr int SW = TW + 4, SH = TH + 4;            // u_sigma on tile +- 2
+    constexpr int QW = TW + 2, QH = TH + 2;            // tile +- 1
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sxw = reinterpret_cast<T *>(smem_raw);
+    T *sv = sxw + XW * XH;
+    T *sxp = sv + VW * VH;     // x pass: XH rows x SW columns
+    T *ss = sxp + XH * SW;     // u_sigma
+    T *tw = ss + SW * SH;      // T_w = D : H(v), 3 planes on tile +- 1
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int w = a.w, h = a.h;
+    const long pitch = a.pitch;
+    for (int i = tid; i < XW * XH; i += 256) {
+        int r = i / XW, c = i - r * XW;
+        sxw[i] = a.x[(long)mirror_idx(y0 - HL + r, h) * pitch + mirror_idx(x0 - HL + c, w)];
+    }
+    for (int i = tid; i < VW * VH; i += 256) {
+        int r = i / VW, c = i - r * VW;
+        long gi = (long)mirror_idx(y0 - 2 + r, h) * pitch + mirror_idx(x0 - 2 + c, w);
+        sv[i] = a.mask[gi] ? T(0) : a.g[gi];
+    }
+    __syncthreads();
+    for (int i = tid; i < XH * SW; i += 256) {  // Gaussian x pass
+        int r = i / SW, c = i - r * SW;
+        const T *row = sxw + r * XW + c;
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) acc += a.wts[t] * row[t];
+        sxp[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < SW * SH; i += 256) {  // Gaussian y pass
+        int r = i / SW, c = i - r * SW;
+        const T *col = sxp + r * SW + c;
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) acc += a.wts[t] * col[t * SW];
+        ss[i] = acc;
+    }
+    __syncthreads();
+    constexpr int PL = QW * QH;
+    const T l2 = a.l2;
+    for (int i = tid; i < PL; i += 256) {
+        int r = i / QW, c = i - r * QW;  // tile (r-1, c-1)
+        const T *s0 = ss + (r + 1) * SW + (c + 1);
+        const T gx = (s0[1] - s0[-1]) * T(0.5), gy = (s0[SW] - s0[-SW]) * T(0.5);
+        const T rho2 = gx * gx + gy * gy;
+        const T sq = sqrt(T(1) + rho2 / l2);  // 1 / mu1
+        const T mu1 = T(1) / sq, mu3 = sqrt(mu1);
+        T C, S;
+        if (rho2 == T(0)) { C = T(1); S = T(0); }
+        else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
+        const T *x0p = sxw + (r + 1 + R) * XW + (c + 1 + R);
+        const T *v0 = sv + (r + 1) * VW + (c + 1);
+        const T hxx = (x0p[-1] + x0p[1]) - T(2) * x0p[0];
+        const T hyy = (x0p[-XW] + x0p[XW]) - T(2) * x0p[0];
+        const T hxy = ((x0p[XW + 1] + x0p[-XW - 1]) - (x0p[XW - 1] + x0p[-XW + 1])) * T(0.25);
+        const T wxx = (v0[-1] + v0[1]) - T(2) * v0[0];
+        const T wyy = (v0[-VW] + v0[VW]) - T(2) * v0[0];
+        const T wxy = ((v0[VW + 1] + v0[-VW - 1]) - (v0[VW - 1] + v0[-VW + 1])) * T(0.25);
+        // rotated frame (double angle C = cos 2t, S = sin 2t)
+        const T Ah = (hxx + hyy) * T(0.5), Bh = (hxx - hyy) * T(0.5);
+        const T Aw = (wxx + wyy) * T(0.5), Bw = (wxx - wyy) * T(0.5);
+        const T h11 = Ah + C * Bh + S * hxy, h22 = Ah - C * Bh - S * hxy, h12 = C * hxy - S * Bh;
+        const T w11 = Aw + C * Bw + S * wxy, w22 = Aw - C * Bw - S * wxy, w12 = C * wxy - S * Bw;
+        // T_w = D : W  (the frozen-tensor part applies P(x) to v)
+        {
+            const T pp = mu1 * w11, qq = w22, rr = mu3 * w12;
+            const T hs = (pp + qq) * T(0.5), hd = (pp - qq) * T(0.5);
+            tw[i] = hs + C * hd - S * rr;
+            tw[PL + i] = S * hd + C * rr;
+            tw[2 * PL + i] = hs - C * hd + S * rr;
+        }
+        // q = d s / d g for s = W : D(g) : H = W:H + (mu1-1) w11 h11 + 2 (mu3-1) w12 h12
+        if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
+            const int gxp = x0 + c - 1, gyp = y0 + r - 1;
+            if (gxp < w && gyp < h) {
+                const T dmu1 = -mu1 * mu1 * mu1 / (T(2) * l2);  // d mu1 / d rho^2
+                const T dmu3 = dmu1 / (T(2) * mu3);
+                const T srho = dmu1 * w11 * h11 + T(2) * dmu3 * w12 * h12;  // d s / d rho^2
+                const T rs = sqrt(sq);
+                const T c1 = T(1) / (l2 * sq * (sq + T(1)));             // (1 - mu1) / rho^2
+                const T c3 = T(1) / (l2 * (sq + T(1)) * rs * (rs + T(1)));  // (1 - mu3) / rho^2
+                const T th = -c1 * T(2) * (w12 * h11 + w11 * h12) - T(2) * c3 * (-(w11 - w22) * h12 - w12 * (h11 - h22));
+                const long gi = (long)gyp * pitch + gxp;
+                a.qx[gi] = T(2) * gx * srho - gy * th;
+                a.qy[gi] = T(2) * gy * srho + gx * th;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < TW * TH; i += 256) {  // P(x) v: outer divergence of T_w
+        int r = i / TW, c = i - r * TW;
+        int gxp = x0 + c, gyp = y0 + r;
+        if (gxp >= w || gyp >= h) continue;
+        const int k = (r + 1) * QW + (c + 1);
+        const T *txx = tw, *txy = tw + PL, *tyy = tw + 2 * PL;
+        const T dxx = (txx[k - 1] + txx[k + 1]) - T(2) * txx[k];
+        const T dyy = (tyy[k - QW] + tyy[k + QW]) - T(2) * tyy[k];
+        const T dxy = ((txy[k + QW + 1] + txy[k - QW - 1]) - (txy[k + QW - 1] + txy[k - QW + 1])) * T(0.5);
+        a.pv[(long)gyp * pitch + gxp] = (dxx + dyy) + dxy;
+    }
+}
+
+// -D_odd q at pixel (x, y): the transpose of the central-difference gradient
+// (q_x odd across the left/right border, q_y across the top/bottom border).
+template <typename T>
+__device__ __forceinline__ T adj_divq(const AdjArgs<T> &a, int x, int y)
+{
+    const long row = (long)y * a.pitch;
+    const T xr = x + 1 < a.w ? a.qx[row + x + 1] : -a.qx[row + x];
+    const T xl = x - 1 >= 0 ? a.qx[row + x - 1] : -a.qx[row + x];
+    const T yd = y + 1 < a.h ? a.qy[row + a.pitch + x] : -a.qy[row + x];
+    const T yu = y - 1 >= 0 ? a.qy[row - a.pitch + x] : -a.qy[row + x];
+    return -((xr - xl) + (yd - yu)) * T(0.5);
+}
+
+// B2: z = G (-D_odd q), then the step's adjoint recursion at every pixel of a tile.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
+{
+    constexpr int TW = kAdjTW, TH = kAdjTH;
+    constexpr int RW = TW + 2 * R, RH = TH + 2 * R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sr = reinterpret_cast<T *>(smem_raw);  // -D_odd q on tile +- R (mirrored outside the image)
+    T *sxp = sr + RW * RH;                    // x pass: RH rows x TW columns
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    for (int i = tid; i < RW * RH; i += 256) {
+        int r = i / RW, c = i - r * RW;
+        sr[i] = adj_divq(a, mirror_idx(x0 - R + c, a.w), mirror_idx(y0 - R + r, a.h));
+    }
+    __syncthreads();
+    for (int i = tid; i < RH * TW; i += 256) {
+        int r = i / TW, c = i - r * TW;
+        const T *row = sr + r * RW + c;
+        T acc = T(0);
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) acc += a.wts[t] * row[t];
+        sxp[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < TW * TH; i += 256) {
+        int r = i / TW, c = i - r * TW;
+        int gxp = x0 + c, gyp = y0 + r;
+        if (gxp >= a.w || gyp >= a.h) continue;
+        const T *col = sxp + r * TW + c;
+        T z = T(0);
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) z += a.wts[t] * col[t * TW];
+        const long gi = (long)gyp * a.pitch + gxp;
+        const T gv = a.g[gi];
+        const bool known = a.mask[gi] != 0;
+        const T v = known ? T(0) : gv;
+        const T jt = a.pv[gi] + z;  // J_F(x)^T v
+        const T dcur = (known ? gv : T(0)) + a.alpha * v - a.alpha * a.tau * jt;
+        const T dprev = (T(1) - a.alpha) * v;
+        const T pe = a.pend[gi];
+        if (a.first_of_cycle) {
+            a.gout[gi] = pe + dcur + dprev;
+            a.pend[gi] = T(0);
+        } else {
+            a.gout[gi] = pe + dcur;
+            a.pend[gi] = dprev;
+        }
+    }
+}
+
+template <typename T, int R>
+struct AdjSmem {
+    static constexpr int HL = R + 2;
+    static constexpr size_t B1 = sizeof(T) * ((kAdjTW + 2 * HL) * (kAdjTH + 2 * HL) + (kAdjTW + 4) * (kAdjTH + 4) +
+                                              (kAdjTH + 2 * HL) * (kAdjTW + 4) + (kAdjTW + 4) * (kAdjTH + 4) +
+                                              3 * (kAdjTW + 2) * (kAdjTH + 2));
+    static constexpr size_t B2 = sizeof(T) * ((kAdjTW + 2 * R) * (kAdjTH + 2 * R) + (kAdjTH + 2 * R) * kAdjTW);
+};
+
+template <typename T, int R>
+cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
+{
+    using SM = AdjSmem<T, R>;
+    if (!ap) {
+        cudaError_t e = cudaFuncSetAttribute(adj_b1_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(adj_b2_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
+    }
+    dim3 grid((ap->w + kAdjTW - 1) / kAdjTW, (ap->h + kAdjTH - 1) / kAdjTH);
+    adj_b1_kernel<T, R><<<grid, 256, SM::B1, s>>>(*ap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adj_b2_kernel<T, R><<<grid, 256, SM::B2, s>>>(*ap);
+    return cudaGetLastError();
+}
+
+}  // namespace foeed

@@ -13,9 +13,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "dispatch.h"
 #include "foeed.h"
 
@@ -571,6 +573,223 @@ const char *foeed_last_error(void) { return g_err; }
 const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint of the solve (gradient with respect to the stored grey values).
+
+namespace {
+
+struct VjpLayout {
+    Layout base;          // control block, partials, C/A/B, mask of the forward solve
+    size_t img;           // bytes of one internal image
+    size_t cp, seg, g, pend, pv, qx, qy, total;
+    int ncp, K;
+};
+
+VjpLayout vjp_layout(int w, int h, foeed_dtype d, const foeed_params &p, int K)
+{
+    VjpLayout V;
+    V.base = layout(w, h, d);
+    V.img = align_up((size_t)h * V.base.P * elem_size(d), kAlign);
+    const long S = (long)p.cycle_len * p.max_cycles;
+    V.K = K;
+    V.ncp = (int)((S + K - 1) / K);
+    size_t off = V.base.total;
+    V.cp = off; off += V.img * 2 * (size_t)V.ncp;  // (u^s, u^{s-1}) at s = 0, K, 2K, ...
+    V.seg = off; off += V.img * (size_t)K;           // states of one segment
+    V.g = off; off += V.img;
+    V.pend = off; off += V.img;
+    V.pv = off; off += V.img;
+    V.qx = off; off += V.img;
+    V.qy = off; off += V.img;
+    V.total = off;
+    return V;
+}
+
+foeed_status check_vjp(const foeed_params *params, foeed_dtype d, int K)
+{
+    foeed_status st;
+    if ((st = check_params(params, true))) return st;
+    if (d != FOEED_F32 && d != FOEED_F64) return fail(FOEED_ERR_ARG, "the adjoint runs FOEED_F32 or FOEED_F64");
+    if (params->diffusivity != 0 || params->mu3_mode != 0)
+        return fail(FOEED_ERR_ARG, "the adjoint needs the Charbonnier diffusivity and mu3 = sqrt(mu1)");
+    if (params->tol != 0.0) return fail(FOEED_ERR_ARG, "the adjoint differentiates a fixed number of cycles (tol = 0)");
+    if (params->init_mode != 0) return fail(FOEED_ERR_ARG, "the adjoint needs init_mode 0");
+    if (K < 1) return fail(FOEED_ERR_ARG, "checkpoint_every must be >= 1");
+    return FOEED_OK;
+}
+
+template <typename T>
+__global__ void pitch_copy_kernel(const T *__restrict__ src, long sp, T *__restrict__ dst, long dp, int w, int h)
+{
+    const long n = (long)w * h;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        dst[y * dp + x] = src[y * sp + x];
+    }
+}
+
+// Sum of the adjoint over the unknown pixels (the mean initialisation path).
+template <typename T>
+__global__ void unknown_sum_kernel(const T *__restrict__ g, const uint8_t *__restrict__ mi, int w, int h, long P,
+                                   Ctl *ctl, double *partials)
+{
+    __shared__ double red[64];
+    double s = 0.0, c = 0.0;
+    const long n = (long)w * h;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        if (!mi[y * P + x]) { s += double(g[y * P + x]); c += 1.0; }
+    }
+    if (grid_sum2_last(s, c, partials, &ctl->ticket, gridDim.x, blockIdx.x, red)) ctl->err[0] = s;
+}
+
+// grad_f = M g + (sum over unknown pixels of g) / |K| on the known pixels.
+template <typename T>
+__global__ void grad_f_kernel(const T *__restrict__ g, const uint8_t *__restrict__ mi, int w, int h, long P,
+                              T *__restrict__ gf, long pitch, const Ctl *ctl)
+{
+    const long n = (long)w * h;
+    const double add = ctl->known > 0 ? ctl->err[0] / double(ctl->known) : 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        long y = i / w, x = i - y * w;
+        gf[y * pitch + x] = mi[y * P + x] ? T(double(g[y * P + x]) + add) : T(0);
+    }
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const AdjArgs<T> *a, int R, cudaStream_t s);
+template <>
+cudaError_t launch_adjoint<float>(const AdjArgs<float> *a, int R, cudaStream_t s) { return adjoint_step_f32(a, R, s); }
+template <>
+cudaError_t launch_adjoint<double>(const AdjArgs<double> *a, int R, cudaStream_t s) { return adjoint_step_f64(a, R, s); }
+
+template <typename T>
+foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, void *grad_f, void *u_out, int w, int h,
+                     long pitch, foeed_dtype d, const foeed_params &p, int K, char *ws, const VjpLayout &V,
+                     cudaStream_t s)
+{
+    const Layout &L = V.base;
+    const long P = L.P;
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    double *partials = reinterpret_cast<double *>(ws + L.partials);
+    const uint8_t *mi = reinterpret_cast<const uint8_t *>(ws + L.mask);
+    T *buf[3] = {reinterpret_cast<T *>(ws + L.bufC), reinterpret_cast<T *>(ws + L.bufA),
+                 reinterpret_cast<T *>(ws + L.bufB)};
+    auto img = [&](size_t off, size_t i) { return reinterpret_cast<T *>(ws + off + V.img * i); };
+    const int n = p.cycle_len;
+    const long S = (long)n * p.max_cycles;
+    const double tau = default_tau(false, p.tau);
+    const int R = gauss_radius(p.sigma);
+    const size_t ibytes = (size_t)h * P * sizeof(T);
+    const int g1 = grid_for((long)w * h);
+
+    Ctl h0;
+    std::memset(&h0, 0, sizeof(h0));
+    CK(cudaMemcpyAsync(ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(launch_step(false, d, nullptr, p, s));
+    CK(launch_adjoint<T>(nullptr, R, s));
+    CK(launch_prep<T>(f, mask, nullptr, w, h, pitch, L, ws, 0, s));  // C = u^{0,0}
+
+    auto fwd_step = [&](const T *prev, const T *cur, T *next, long st) -> cudaError_t {
+        StepCall c{};
+        const int k = (int)(st % n);
+        c.uprev = prev; c.ucur = cur; c.unext = next; c.mask = mi;
+        c.w = w; c.h = h; c.pitch = P;
+        c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
+        c.tau = tau;
+        return launch_step(false, d, &c, p, s);
+    };
+
+    // forward solve with checkpoints of (u^s, u^{s-1}) every K steps
+    int icur = 0, iprev = 0;
+    for (long st = 0; st < S; ++st) {
+        const int k = (int)(st % n);
+        if (k == 0) iprev = icur;
+        if (st % K == 0) {
+            CK(cudaMemcpyAsync(img(V.cp, 2 * (st / K)), buf[icur], ibytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(img(V.cp, 2 * (st / K) + 1), buf[iprev], ibytes, cudaMemcpyDeviceToDevice, s));
+        }
+        int inext = 0;
+        while (inext == icur || inext == iprev) ++inext;
+        CK(fwd_step(buf[iprev], buf[icur], buf[inext], st));
+        iprev = icur;
+        icur = inext;
+    }
+    if (u_out)
+        pitch_copy_kernel<T><<<g1, kRedThreads, 0, s>>>(buf[icur], P, static_cast<T *>(u_out), pitch, w, h);
+
+    // backward: g = dL/du_final, then the segments in reverse
+    T *g = img(V.g, 0), *pend = img(V.pend, 0);
+    pitch_copy_kernel<T><<<g1, kRedThreads, 0, s>>>(static_cast<const T *>(grad_u), pitch, g, P, w, h);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(pend, 0, ibytes, s));
+    AdjArgs<T> a{};
+    a.g = g; a.gout = g; a.pend = pend; a.mask = mi;
+    a.pv = img(V.pv, 0); a.qx = img(V.qx, 0); a.qy = img(V.qy, 0);
+    a.w = w; a.h = h; a.pitch = P;
+    a.tau = T(tau);
+    a.l2 = T(p.lambda * p.lambda);
+    gauss_taps<T>(p.sigma, a.wts);
+    for (int seg = V.ncp - 1; seg >= 0; --seg) {
+        const long s0 = (long)seg * K, s1 = std::min<long>(S, s0 + K);
+        // states u^{s0} .. u^{s1-1} of this segment, recomputed from its checkpoint
+        CK(cudaMemcpyAsync(img(V.seg, 0), img(V.cp, 2 * seg), ibytes, cudaMemcpyDeviceToDevice, s));
+        for (long st = s0; st + 1 < s1; ++st) {
+            const int k = (int)(st % n);
+            const T *cur = img(V.seg, st - s0);
+            const T *prev = k == 0 ? cur : (st == s0 ? img(V.cp, 2 * seg + 1) : img(V.seg, st - s0 - 1));
+            CK(fwd_step(prev, cur, img(V.seg, st - s0 + 1), st));
+        }
+        for (long st = s1 - 1; st >= s0; --st) {
+            const int k = (int)(st % n);
+            a.x = img(V.seg, st - s0);
+            const double al = (4.0 * k + 2.0) / (2.0 * k + 3.0);
+            a.alpha = T(al);
+            a.first_of_cycle = k == 0;
+            CK(launch_adjoint<T>(&a, R, s));
+        }
+    }
+    // grad_f = M g + mean-path term (the control block still holds |K| from the set-up)
+    unknown_sum_kernel<T><<<g1, kRedThreads, 0, s>>>(g, mi, w, h, P, ctl, partials);
+    CK(cudaGetLastError());
+    grad_f_kernel<T><<<g1, kRedThreads, 0, s>>>(g, mi, w, h, P, static_cast<T *>(grad_f), pitch, ctl);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    (void)buf;
+    return FOEED_OK;
+}
+
+}  // namespace
+
+extern "C" size_t foeed_vjp_workspace_bytes(int w, int h, foeed_dtype dtype, const foeed_params *params,
+                                            int checkpoint_every)
+{
+    if (w < 1 || h < 1 || !params || checkpoint_every < 1 || params->cycle_len < 1 || params->max_cycles < 1) return 0;
+    return vjp_layout(w, h, dtype, *params, checkpoint_every).total;
+}
+
+extern "C" foeed_status foeed_inpaint_vjp(const void *f, const uint8_t *mask, const void *grad_u, void *grad_f,
+                                          void *u_out, int w, int h, long pitch, foeed_dtype dtype,
+                                          const foeed_params *params, int checkpoint_every, void *workspace,
+                                          size_t workspace_bytes, void *stream)
+{
+    foeed_status st = check_image(w, h, pitch, dtype);
+    if (st) return st;
+    if ((st = check_vjp(params, dtype, checkpoint_every))) return st;
+    if (!f || !mask || !grad_u || !grad_f || !workspace) return fail(FOEED_ERR_ARG, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(FOEED_ERR_ARG, "workspace must be 256-byte aligned");
+    const VjpLayout V = vjp_layout(w, h, dtype, *params, checkpoint_every);
+    if (workspace_bytes < V.total) return fail(FOEED_ERR_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, V.total);
+    char *ws = static_cast<char *>(workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = dtype == FOEED_F64 ? run_vjp<double>(f, mask, grad_u, grad_f, u_out, w, h, pitch, dtype, *params,
+                                              checkpoint_every, ws, V, s)
+                            : run_vjp<float>(f, mask, grad_u, grad_f, u_out, w, h, pitch, dtype, *params,
+                                             checkpoint_every, ws, V, s);
+    if (st == FOEED_OK) g_err[0] = 0;
+    return st;
+}
 
 // ---------------------------------------------------------------------------
 // Batched solve: many images, one launch per FSI step over all their tiles.
