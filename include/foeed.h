@@ -162,6 +162,14 @@ foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dt
                                  const foeed_params *params, void *workspace, size_t workspace_bytes,
                                  void *stream, foeed_report *reports);
 
+/* The batched solve with second-order EED (Eq. EEDModel); same contract and
+ * workspace as foeed_inpaint_batch, tau <= 0 selects 0.25, mu3_mode ignored.
+ * The channel-wise colour reconstructions of Sec. 5 are batches of this form:
+ * one instance per channel, all sharing the mask. */
+foeed_status eed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
+                               const foeed_params *params, void *workspace, size_t workspace_bytes,
+                               void *stream, foeed_report *reports);
+
 /* Workspace bytes foeed_inpaint_vjp needs (checkpoint every `checkpoint_every` steps). */
 size_t foeed_vjp_workspace_bytes(int w, int h, foeed_dtype dtype, const foeed_params *params,
                                  int checkpoint_every);
@@ -184,6 +192,21 @@ size_t foeed_vjp_workspace_bytes(int w, int h, foeed_dtype dtype, const foeed_pa
 foeed_status foeed_inpaint_vjp(const void *f, const uint8_t *mask, const void *grad_u, void *grad_f, void *u_out,
                                int w, int h, long pitch, foeed_dtype dtype, const foeed_params *params,
                                int checkpoint_every, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * The paper's unifying fourth-order operator (Eq. gen4thPDE_Model) with
+ * caller-supplied coefficients: Pu = sum_ij d_ij [ sum_kl d_ijkl u_kl ], so that
+ * du/dt = -Pu. FOEED (Eq. genModel), You-Kaveh, Hajiaboli and Li et al.
+ * (Sec. 3.2) are particular fields d.
+ *   u   [h x pitch] image;  Pu [h x pitch] output (must not alias u)
+ *   d   [h x pitch x 16] coefficients, d[(y*pitch + x)*16 + ((i*2+j)*2+k)*2+l],
+ *       index 0 = x, 1 = y; need not be symmetric.
+ * Stencils of Sec. 3.3; u mirrored at the border, T_xx and T_yy mirrored,
+ * T_xy and T_yx odd across each border. FOEED_F32 or FOEED_F64.
+ * Asynchronous on `stream`.
+ */
+foeed_status foeed_apply_tensor_field(const void *u, const void *d, void *Pu, int w, int h, long pitch,
+                                      foeed_dtype dtype, void *stream);
 
 /* Bytes of workspace foeed_errors needs for a w x h image. */
 size_t foeed_errors_workspace_bytes(int w, int h);

@@ -22,8 +22,9 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "foeed_inpaint_vjp", "foeed_inpaint_diff",
-           "foeed_step", "eed_step", "foeed_errors", "workspace_bytes",
+__all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "eed_inpaint_batch", "inpaint_channels",
+           "foeed_inpaint_vjp", "foeed_inpaint_diff",
+           "foeed_step", "eed_step", "foeed_errors", "foeed_apply_tensor_field", "workspace_bytes",
            "Report", "FoeedError", "lib", "F32", "F64", "F32_F64U", "STATUS"]
 
 F32, F64, F32_F64U = 0, 1, 2
@@ -88,13 +89,16 @@ def lib():
             fn.restype = i
         L.foeed_batch_workspace_bytes.argtypes = [C.POINTER(_Instance), i, i]
         L.foeed_batch_workspace_bytes.restype = sz
-        L.foeed_inpaint_batch.argtypes = [C.POINTER(_Instance), i, i, C.POINTER(_Params), vp, sz, vp,
-                                          C.POINTER(_Report)]
-        L.foeed_inpaint_batch.restype = i
+        for name in ("foeed_inpaint_batch", "eed_inpaint_batch"):
+            fn = getattr(L, name)
+            fn.argtypes = [C.POINTER(_Instance), i, i, C.POINTER(_Params), vp, sz, vp, C.POINTER(_Report)]
+            fn.restype = i
         L.foeed_vjp_workspace_bytes.argtypes = [i, i, i, C.POINTER(_Params), i]
         L.foeed_vjp_workspace_bytes.restype = sz
         L.foeed_inpaint_vjp.argtypes = [vp, vp, vp, vp, vp, i, i, C.c_long, i, C.POINTER(_Params), i, vp, sz, vp]
         L.foeed_inpaint_vjp.restype = i
+        L.foeed_apply_tensor_field.argtypes = [vp, vp, vp, i, i, C.c_long, i, vp]
+        L.foeed_apply_tensor_field.restype = i
         L.foeed_errors_workspace_bytes.argtypes = [i, i]
         L.foeed_errors_workspace_bytes.restype = sz
         L.foeed_errors.argtypes = [vp, vp, i, i, C.c_long, i, vp, sz, vp, C.POINTER(C.c_double)]
@@ -226,12 +230,36 @@ def eed_inpaint(f, mask, lam, sigma, cycle_len, max_cycles, **kw):
     return _inpaint(1, f, mask, lam, sigma, cycle_len, max_cycles, **kw)
 
 
-def foeed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, tau=0.0, tol=0.0, init_mode=0,
-                        dtype="f32", check_every=8, stream=None, workspace=None, raise_on_status=True):
+def foeed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, **kw):
     """Batched FOEED solve of many images of uneven sizes (one launch per FSI step over
     all their tiles, one captured graph per cycle). images/masks: lists of 2-D CUDA
     tensors (float32 / uint8, unit column stride); lambdas: one contrast parameter per
-    image. Returns (list of result tensors, list of Report)."""
+    image. Keywords: tau, tol, init_mode, dtype ("f32" / "f32_f64u"), check_every,
+    stream, workspace, raise_on_status. Returns (list of result tensors, list of Report)."""
+    return _inpaint_batch("foeed_inpaint_batch", images, masks, lambdas, sigma, cycle_len, max_cycles, **kw)
+
+
+def eed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, **kw):
+    """Batched second-order EED solve (Eq. EEDModel); same arguments as foeed_inpaint_batch."""
+    return _inpaint_batch("eed_inpaint_batch", images, masks, lambdas, sigma, cycle_len, max_cycles, **kw)
+
+
+def inpaint_channels(image, mask, lam, sigma, cycle_len, max_cycles, method="foeed", **kw):
+    """Channel-wise reconstruction of a multi-channel image (Sec. 5, colour images):
+    image [C, h, w] float32 CUDA tensor, one mask [h, w] shared by all channels, one
+    batched solve with one instance per channel. Returns ([C, h, w] result, reports)."""
+    torch = _torch()
+    if not (isinstance(image, torch.Tensor) and image.is_cuda and image.dim() == 3):
+        raise FoeedError(1, "image must be a [C, h, w] CUDA tensor")
+    chans = [image[c].contiguous() for c in range(image.shape[0])]
+    m = mask.to(image.device, torch.uint8).contiguous()
+    fn = {"foeed": foeed_inpaint_batch, "eed": eed_inpaint_batch}[method]
+    outs, reps = fn(chans, [m] * len(chans), [lam] * len(chans), sigma, cycle_len, max_cycles, **kw)
+    return torch.stack(outs), reps
+
+
+def _inpaint_batch(entry, images, masks, lambdas, sigma, cycle_len, max_cycles, tau=0.0, tol=0.0, init_mode=0,
+                   dtype="f32", check_every=8, stream=None, workspace=None, raise_on_status=True):
     torch = _torch()
     count = len(images)
     if not (len(masks) == len(lambdas) == count) or count == 0:
@@ -261,8 +289,8 @@ def foeed_inpaint_batch(images, masks, lambdas, sigma, cycle_len, max_cycles, ta
     p = _params(1.0, sigma, tau, cycle_len, max_cycles, tol, 0, 0, init_mode, check_every)
     reps = (_Report * count)()
     with torch.cuda.device(dev):
-        st = lib().foeed_inpaint_batch(arr, count, code, C.byref(p), C.c_void_p(workspace.data_ptr()),
-                                       workspace.numel(), _stream_ptr(stream), reps)
+        st = getattr(lib(), entry)(arr, count, code, C.byref(p), C.c_void_p(workspace.data_ptr()),
+                                   workspace.numel(), _stream_ptr(stream), reps)
     if st not in (0, 3, 4) or (raise_on_status and st != 0):
         _check(st)
     reports = [Report(st, r.cycles_run, r.last_rel_change, bool(r.converged), r.ms) for r in reps]
@@ -370,6 +398,23 @@ def foeed_step(u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw):
 def eed_step(u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw):
     """One masked EED FSI step into u_next."""
     return _step(1, u_prev, u_cur, u_next, mask, alpha, lam, sigma, **kw)
+
+
+def foeed_apply_tensor_field(u, d, stream=None):
+    """Pu = sum_ij d_ij [d_ijkl u_kl] for a coefficient field d of shape [h, w, 2, 2, 2, 2]
+    (Eq. gen4thPDE_Model; du/dt = -Pu). u: 2-D CUDA tensor (float32 / float64)."""
+    torch = _torch()
+    if not (u.is_cuda and u.dim() == 2):
+        raise FoeedError(1, "u must be a 2-D CUDA tensor")
+    u = u.contiguous()
+    h, w = u.shape
+    d = d.to(u.device, u.dtype).reshape(h, w, 16).contiguous()
+    out = torch.empty_like(u)
+    code = F64 if u.dtype == torch.float64 else F32
+    with torch.cuda.device(u.device):
+        _check(lib().foeed_apply_tensor_field(C.c_void_p(u.data_ptr()), C.c_void_p(d.data_ptr()),
+                                              C.c_void_p(out.data_ptr()), w, h, w, code, _stream_ptr(stream)))
+    return out
 
 
 def foeed_errors(u, v, dtype=None, stream=None):

@@ -568,6 +568,18 @@ foeed_status foeed_errors(const void *u, const void *v, int w, int h, long pitch
     return FOEED_OK;
 }
 
+foeed_status foeed_apply_tensor_field(const void *u, const void *d, void *Pu, int w, int h, long pitch,
+                                      foeed_dtype dtype, void *stream)
+{
+    foeed_status st = check_image(w, h, pitch, dtype);
+    if (st) return st;
+    if (dtype == FOEED_F32_F64U) return fail(FOEED_ERR_ARG, "use FOEED_F32 or FOEED_F64");
+    if (!u || !d || !Pu) return fail(FOEED_ERR_ARG, "NULL pointer");
+    if (Pu == u) return fail(FOEED_ERR_ARG, "Pu must not alias u");
+    CK(apply_field(u, d, Pu, w, h, pitch, dtype == FOEED_F64, static_cast<cudaStream_t>(stream)));
+    return FOEED_OK;
+}
+
 const char *foeed_last_error(void) { return g_err; }
 
 const char *foeed_version(void) { return "foeed-gb300 0.1 (sm_103a)"; }
@@ -843,16 +855,17 @@ extern "C" size_t foeed_batch_workspace_bytes(const foeed_instance *inst, int co
     return bp.total;
 }
 
-extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
-                                            const foeed_params *params, void *workspace, size_t workspace_bytes,
-                                            void *stream, foeed_report *reports)
+static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int count, foeed_dtype dtype,
+                                  const foeed_params *params, void *workspace, size_t workspace_bytes, void *stream,
+                                  foeed_report *reports)
 {
+    auto batch_step = eed ? batch_step_fast_eed_f32 : batch_step_fast_foeed_f32;
     foeed_status st;
     if ((st = check_params(params, true))) return st;
     const foeed_params &p = *params;
     if (dtype != FOEED_F32 && dtype != FOEED_F32_F64U)
         return fail(FOEED_ERR_ARG, "the batched solver runs FOEED_F32 or FOEED_F32_F64U");
-    if (!fast_params(false, p))
+    if (!fast_params(eed, p))
         return fail(FOEED_ERR_ARG, "the batched solver needs the Charbonnier diffusivity and mu3 = sqrt(mu1)");
     if (p.cycle_len < 2) return fail(FOEED_ERR_ARG, "the batched solver needs cycle_len >= 2");
     BatchPlan bp;
@@ -870,7 +883,7 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
     char *ws = static_cast<char *>(workspace);
     const bool f64u = dtype == FOEED_F32_F64U;
     const int R = gauss_radius(p.sigma);
-    const double tau = default_tau(false, p.tau);
+    const double tau = default_tau(eed, p.tau);
 
     // device tables: one entry per image, one (image, tile) pair per CTA
     std::vector<BatchInst> hi(count);
@@ -901,9 +914,17 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
     Ctl h0;
     std::memset(&h0, 0, sizeof(h0));
     h0.tol = p.tol;
-    cudaEvent_t ev0, ev1;
-    CK(cudaEventCreate(&ev0));
-    CK(cudaEventCreate(&ev1));
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    CK(cudaEventCreate(&evs.e[0]));
+    CK(cudaEventCreate(&evs.e[1]));
+    cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1];
     CK(cudaEventRecord(ev0, s));
     for (int i = 0; i < count; ++i) {
         CK(cudaMemcpyAsync(hi[i].ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -916,7 +937,7 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
     c.w = 1; c.h = 1; c.pitch = 4;
     c.tau = tau;
     StepArgs<float> a = make_args<float>(c, p);
-    CK(batch_step_fast_foeed_f32(nullptr, nullptr, 0, R, f64u, s));
+    CK(batch_step(nullptr, nullptr, 0, R, f64u, s));
     int dev = 0;
     CK(cudaGetDevice(&dev));
     cudaStream_t cs = g_capture_stream[dev & 63];
@@ -937,7 +958,7 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
         a.alpha_t = float(a.alpha);
         a.residual = b.last;
         a.pdl = k > 0;
-        err = batch_step_fast_foeed_f32(&a, &b, bp.ntiles, R, f64u, cs);
+        err = batch_step(&a, &b, bp.ntiles, R, f64u, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -975,8 +996,6 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
     if (err != cudaSuccess) return fail(FOEED_ERR_CUDA, "batched solve: %s", cudaGetErrorString(err));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev0, ev1));
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     for (int i = 0; i < count; ++i) {
         if (reports) {
             reports[i].cycles_run = hc[i].cycles;
@@ -991,6 +1010,20 @@ extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int coun
     }
     if (result == FOEED_OK) g_err[0] = 0;
     return result;
+}
+
+extern "C" foeed_status foeed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
+                                            const foeed_params *params, void *workspace, size_t workspace_bytes,
+                                            void *stream, foeed_report *reports)
+{
+    return inpaint_batch(false, inst, count, dtype, params, workspace, workspace_bytes, stream, reports);
+}
+
+extern "C" foeed_status eed_inpaint_batch(const foeed_instance *inst, int count, foeed_dtype dtype,
+                                          const foeed_params *params, void *workspace, size_t workspace_bytes,
+                                          void *stream, foeed_report *reports)
+{
+    return inpaint_batch(true, inst, count, dtype, params, workspace, workspace_bytes, stream, reports);
 }
 
 // ---------------------------------------------------------------------------

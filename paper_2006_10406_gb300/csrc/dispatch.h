@@ -28,6 +28,8 @@ cudaError_t step_fast_eed_f32(const StepArgs<float> *a, int R, bool f64_update, 
 // only prepares the kernel.
 cudaError_t batch_step_fast_foeed_f32(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R,
                                       bool f64_update, cudaStream_t s);
+cudaError_t batch_step_fast_eed_f32(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R,
+                                    bool f64_update, cudaStream_t s);
 
 // Backward of one masked FOEED FSI step (kernels B1 + B2, adjoint.cuh);
 // a == nullptr only prepares the kernels.
@@ -35,5 +37,8 @@ template <typename T>
 struct AdjArgs;
 cudaError_t adjoint_step_f32(const AdjArgs<float> *a, int R, cudaStream_t s);
 cudaError_t adjoint_step_f64(const AdjArgs<double> *a, int R, cudaStream_t s);
+
+// Fourth-order divergence with a caller-supplied coefficient field (generic_field.cu).
+cudaError_t apply_field(const void *u, const void *d, void *pu, int w, int h, long pitch, bool f64, cudaStream_t s);
 
 }  // namespace foeed

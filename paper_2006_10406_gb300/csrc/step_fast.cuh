@@ -444,9 +444,9 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
 }
 
 // ---------------------------------------------------------------------------
-// Batched FOEED: one launch per FSI step over the tiles of many images.
+// Batched FOEED or EED: one launch per FSI step over the tiles of many images.
 
-template <int R, typename U>
+template <int R, bool EED, typename U>
 __global__ void __launch_bounds__(256) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
 {
     extern __shared__ __align__(16) float sm[];
@@ -472,15 +472,15 @@ __global__ void __launch_bounds__(256) fsi_batch_step_fast(const StepArgs<float>
     im.c4 = I.c4;
     const int ty = tl.y / I.ntx, tx = tl.y - ty * I.ntx;
     double rnum = 0.0, rden = 0.0;
-    fast_tile<R, false, U>(p, im, tx * FastTile<R, false>::TW, ty * FastTile<R, false>::TH, sm, rnum, rden);
+    fast_tile<R, EED, U>(p, im, tx * FastTile<R, EED>::TW, ty * FastTile<R, EED>::TH, sm, rnum, rden);
     if (b.last) finish_cycle_residual(rnum, rden, I.ctl, I.partials, I.ntx * I.nty, tl.y, red);
 }
 
-template <int R, typename U>
+template <int R, bool EED, typename U>
 cudaError_t launch_fsi_batch_step_fast(const StepArgs<float> *ap, const BatchArgs *bp, int ntiles, cudaStream_t s)
 {
-    using G = FastTile<R, false>;
-    auto kern = fsi_batch_step_fast<R, U>;
+    using G = FastTile<R, EED>;
+    auto kern = fsi_batch_step_fast<R, EED, U>;
     if (!ap) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (!ap->pdl) {
         kern<<<ntiles, 256, G::SMEM, s>>>(*ap, *bp);

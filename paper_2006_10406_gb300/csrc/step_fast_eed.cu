@@ -24,4 +24,25 @@ cudaError_t step_fast_eed_f32(const StepArgs<float> *a, int R, bool f64_update, 
     return f64_update ? run<double>(a, R, s) : run<float>(a, R, s);
 }
 
+template <typename U>
+static cudaError_t run_batch(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R, cudaStream_t s)
+{
+    switch (R) {
+    case 0: return launch_fsi_batch_step_fast<0, true, U>(a, b, ntiles, s);
+    case 1: return launch_fsi_batch_step_fast<1, true, U>(a, b, ntiles, s);
+    case 2: return launch_fsi_batch_step_fast<2, true, U>(a, b, ntiles, s);
+    case 3: return launch_fsi_batch_step_fast<3, true, U>(a, b, ntiles, s);
+    case 4: return launch_fsi_batch_step_fast<4, true, U>(a, b, ntiles, s);
+    case 5: return launch_fsi_batch_step_fast<5, true, U>(a, b, ntiles, s);
+    case 6: return launch_fsi_batch_step_fast<6, true, U>(a, b, ntiles, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t batch_step_fast_eed_f32(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R,
+                                    bool f64_update, cudaStream_t s)
+{
+    return f64_update ? run_batch<double>(a, b, ntiles, R, s) : run_batch<float>(a, b, ntiles, R, s);
+}
+
 }  // namespace foeed

@@ -28,13 +28,13 @@ template <typename U>
 static cudaError_t run_batch(const StepArgs<float> *a, const BatchArgs *b, int ntiles, int R, cudaStream_t s)
 {
     switch (R) {
-    case 0: return launch_fsi_batch_step_fast<0, U>(a, b, ntiles, s);
-    case 1: return launch_fsi_batch_step_fast<1, U>(a, b, ntiles, s);
-    case 2: return launch_fsi_batch_step_fast<2, U>(a, b, ntiles, s);
-    case 3: return launch_fsi_batch_step_fast<3, U>(a, b, ntiles, s);
-    case 4: return launch_fsi_batch_step_fast<4, U>(a, b, ntiles, s);
-    case 5: return launch_fsi_batch_step_fast<5, U>(a, b, ntiles, s);
-    case 6: return launch_fsi_batch_step_fast<6, U>(a, b, ntiles, s);
+    case 0: return launch_fsi_batch_step_fast<0, false, U>(a, b, ntiles, s);
+    case 1: return launch_fsi_batch_step_fast<1, false, U>(a, b, ntiles, s);
+    case 2: return launch_fsi_batch_step_fast<2, false, U>(a, b, ntiles, s);
+    case 3: return launch_fsi_batch_step_fast<3, false, U>(a, b, ntiles, s);
+    case 4: return launch_fsi_batch_step_fast<4, false, U>(a, b, ntiles, s);
+    case 5: return launch_fsi_batch_step_fast<5, false, U>(a, b, ntiles, s);
+    case 6: return launch_fsi_batch_step_fast<6, false, U>(a, b, ntiles, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -380,3 +380,61 @@ def test_batch_rejects_unsupported_configurations():
         fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 1, 2)
     with pytest.raises(fg.FoeedError):
         fg.foeed_inpaint_batch(imgs, masks, [-1.0], 1.0, 4, 2)
+
+
+@pytest.mark.parametrize("n", [2, 7])
+def test_eed_batch_equals_single_image_solves(n):
+    imgs, masks, lams = _batch_case(seed=90)
+    outs, reps = fg.eed_inpaint_batch(imgs, masks, lams, 1.0, n, 3)
+    for f, m, lam, u, r in zip(imgs, masks, lams, outs, reps):
+        ref, rr = fg.eed_inpaint(f, m, lam, 1.0, n, 3)
+        assert torch.equal(u, ref), float((u - ref).abs().max())
+        assert r.last_rel_change == rr.last_rel_change
+
+
+def test_eed_batch_matches_oracle():
+    imgs, masks, lams = _batch_case(seed=95, sizes=((40, 56), (23, 31)))
+    outs, _ = fg.eed_inpaint_batch(imgs, masks, lams, 1.0, 8, 3)
+    for f, m, lam, u in zip(imgs, masks, lams, outs):
+        ref, _, _ = O.inpaint(1, f.double().cpu().numpy(), m.cpu().numpy(), 1.0, lam, 8, 3)
+        assert np.max(np.abs(u.double().cpu().numpy() - ref)) <= 2e-4
+
+
+@pytest.mark.parametrize("method", ["foeed", "eed"])
+def test_channelwise_colour_reconstruction(method):
+    # three channels sharing one mask (Sec. 5, colour images): each channel of
+    # the batched result equals that channel solved alone, and the oracle
+    img, mask, _ = synth.workload(2, h=45, w=77, instance=7)
+    rgb = np.stack([img, 1.0 - img, np.sqrt(img)]).astype(np.float32)
+    f = torch.from_numpy(rgb).to(DEV)
+    m = torch.from_numpy(mask).to(DEV)
+    out, reps = fg.inpaint_channels(f, m, 0.03, 1.0, 6, 3, method=method)
+    assert out.shape == f.shape and len(reps) == 3
+    single = fg.foeed_inpaint if method == "foeed" else fg.eed_inpaint
+    for c in range(3):
+        ref, _ = single(f[c].contiguous(), m, 0.03, 1.0, 6, 3)
+        assert torch.equal(out[c], ref)
+        oref, _, _ = O.inpaint(0 if method == "foeed" else 1, rgb[c].astype(np.float64), mask, 1.0, 0.03, 6, 3)
+        assert np.max(np.abs(out[c].double().cpu().numpy() - oref)) <= 2e-4
+
+
+# --------------------------------------------------------------------------
+# the unifying fourth-order operator with caller-supplied coefficients
+
+@pytest.mark.parametrize("shape", [(9, 11), (40, 70), (1, 8), (17, 33)])
+def test_apply_tensor_field_matches_oracle(shape):
+    rng = _rng(500 + shape[0])
+    u = rng.uniform(size=shape)
+    d = rng.normal(size=shape + (2, 2, 2, 2))          # arbitrary, not symmetric
+    ref = O.apply_P_field(u, d)
+    got = fg.foeed_apply_tensor_field(_dev(u, torch.float64), torch.from_numpy(d).to(DEV))
+    np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=0, atol=1e-12)
+    got32 = fg.foeed_apply_tensor_field(_dev(u, torch.float32), torch.from_numpy(d).to(DEV))
+    np.testing.assert_allclose(got32.cpu().numpy(), ref, rtol=0, atol=1e-4 * max(1.0, np.abs(ref).max()))
+
+
+def test_apply_tensor_field_with_the_foeed_tensor_is_the_foeed_operator():
+    u = _rng(501).uniform(size=(30, 41))
+    d = O.foeed_tensor_field(u, 1.0, 0.05)
+    got = fg.foeed_apply_tensor_field(_dev(u, torch.float64), torch.from_numpy(d).to(DEV))
+    np.testing.assert_allclose(got.cpu().numpy(), O.foeed_operator(u, 1.0, 0.05), rtol=0, atol=1e-12)
