@@ -39,8 +39,8 @@ WORKLOAD = 3
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel on the full 2048x2048 workload, and the hash of the
 # kernel source it was taken on; reported only while the source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "927827aa0dbfea8365d0e046f5f8b4f09abac11d",
-               "bytes_per_launch": 37788416 + 12800}  # profiles/fsi_step_fast_foeed_f32_r5_2048x2048.md
+NCU_TRAFFIC = {"source_sha1": "6c61f526d78216c1bae1cd3c18f9a26418698e34",
+               "bytes_per_launch": 37793792 + 32256}  # profiles/fsi_step_fast_foeed_f32_r5_2048x2048.md
 
 
 def kernel_source_sha1():
@@ -401,17 +401,39 @@ def main():
         extra["eed"] = {"value": pu_per_solve / (min(eed_ms[1:]) / 1e3), "unit": UNIT,
                         "ms_per_solve": min(eed_ms[1:])}
         if not args.no_accuracy:
+            def timed(fn):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                out = fn()
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                return out[0].clone(), a.elapsed_time(b)
+
             u32, _ = solve()
             u32 = u32.clone()
             ws64 = torch.empty(fg.workspace_bytes(W, H, fg.F64), dtype=torch.uint8, device=dev)
-            u64, _ = fg.foeed_inpaint(fd.double(), md, p["lam"], p["sigma"], n, cycles, workspace=ws64, stream=stream)
+            fd64 = fd.double()
+            fg.foeed_inpaint(fd64, md, p["lam"], p["sigma"], n, 1, workspace=ws64, stream=stream)  # capture
+            u64, ms64 = timed(lambda: fg.foeed_inpaint(fd64, md, p["lam"], p["sigma"], n, cycles, workspace=ws64,
+                                                       stream=stream))
+            fg.foeed_inpaint(fd, md, p["lam"], p["sigma"], n, 1, dtype="f32_f64u", workspace=ws, stream=stream)
+            umx, msmx = timed(lambda: fg.foeed_inpaint(fd, md, p["lam"], p["sigma"], n, cycles, dtype="f32_f64u",
+                                                       workspace=ws, stream=stream))
             imgd = torch.from_numpy(img).to(dev)
             m32 = fg.foeed_errors(u32.double(), imgd)
             m64 = fg.foeed_errors(u64, imgd)
+            mmx = fg.foeed_errors(umx.double(), imgd)
             diff = float((u32.double() - u64).abs().max().item())
             extra["accuracy"] = {"max_abs_f32_vs_f64_gpu": diff, "psnr_f32_db": m32[2], "psnr_f64_db": m64[2],
                                  "psnr_delta_db": abs(m32[2] - m64[2]), "mse_f32": m32[0], "mse_f64": m64[0]}
-            del ws64
+            # the other arithmetic modes of the same solve (the FP64 GPU solve is the parity-tested reference)
+            extra["precisions"] = {
+                "f64": {"value": pu_per_solve / (ms64 / 1e3), "unit": UNIT, "ms_per_solve": ms64},
+                "f32_storage_f64_update": {
+                    "value": pu_per_solve / (msmx / 1e3), "unit": UNIT, "ms_per_solve": msmx,
+                    "max_abs_vs_f64_gpu": float((umx.double() - u64).abs().max().item()),
+                    "psnr_db": mmx[2], "psnr_delta_vs_f64_db": abs(mmx[2] - m64[2])}}
+            del ws64, fd64
             # time to within 1% of the final MSE, FOEED against EED (same workload, FP32)
             def one(method):
                 def run(u0):

@@ -2,15 +2,20 @@
 // mu3 = sqrt(mu1), or EED with Charbonnier g): the hot kernel of the solver.
 //
 // One CTA of 256 threads owns a 64 x 32 output tile. Every stage works on
-// groups of four consecutive pixels of one row (float4 in shared memory), so
-// shared-memory traffic is vectorised and no index needs a division:
+// groups of four consecutive pixels of one row (float4 in shared memory), and
+// each thread keeps a small block of rows or columns in registers so that a
+// shared-memory value is loaded once for several outputs:
 //   A  u^k window, rows tile-(R+2) .. tile+31+(R+2), columns tile-8 .. tile+75
-//      (float4 global loads for interior columns, mirrored scalar loads at the
-//      image border)
-//   B  Gaussian x pass, columns tile-2 .. tile+69, every window row
-//   C  Gaussian y pass, 3 rows per thread, columns tile-2 .. tile+69
-//   D  gradient, mu1/mu3, Hessian and T (FOEED) or the EED fluxes on tile+-1
-//   E  outer divergence, masked FSI update, optional cycle residual, float4 store
+//      (cp.async 16-byte copies for interior columns, mirrored 4-byte copies at
+//      the image border)
+//   B  Gaussian x pass, 8 outputs per item, columns tile-2 .. tile+69, every window row
+//   C  Gaussian y pass, 6 rows per item, columns tile-2 .. tile+65
+//   D  gradient, mu1/mu3, Hessian and T (FOEED) or the EED fluxes on tile+-1,
+//      two rows per item sharing their u_sigma and u rows
+//   E  outer divergence, masked FSI update, optional cycle residual, float4 store;
+//      two rows per thread sharing two T_yy rows
+// The item shapes keep every warp access free of bank conflicts (odd float4
+// row strides, lanes along rows or along column groups).
 // Requirements (checked on the host): row pitch a multiple of 4 elements and
 // 16-byte aligned image and mask pointers.
 #pragma once
@@ -36,6 +41,69 @@ __device__ __forceinline__ float sqrt_fast(float x)
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Eight consecutive floats from shared memory (two float4 loads; s is 16-byte aligned).
+__device__ __forceinline__ void ld8(const float *s, float *o)
+{
+    const float4 a = *reinterpret_cast<const float4 *>(s);
+    const float4 b = *reinterpret_cast<const float4 *>(s + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+
+// One row of four T groups of stage D. sup/sc/sdn: u_sigma rows above/at/below
+// (cols 4q .. 4q+7 of ss: this group's pixels are 1..4), uu/uc/ud: u rows (cols
+// 4q+4 .. 4q+11 of su: pixels 3..6). FOEED writes T_xx, T_xy, T_yy to planes
+// 0..2; EED writes a, c, b d_y u, b d_x u to planes 0..3.
+template <bool EED>
+__device__ __forceinline__ void tensor_row(const float *sup, const float *sc, const float *sdn, const float *uu,
+                                           const float *uc, const float *ud, const float c4, float *dst, const int PL)
+{
+    float o0[4], o1[4], o2[4], o3[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float dx = sc[2 + k] - sc[k];
+        float dy = sdn[1 + k] - sup[1 + k];
+        // A zero gradient gets v1 = (1, 0): the tiny offset leaves every
+        // representable non-negligible dx unchanged.
+        float dxe = dx + 1e-18f;
+        float dxe2 = dxe * dxe;
+        float sq = fmaf(dy, dy, dxe2);          // 4 lambda1
+        float mu1 = rsqrt_fast(fmaf(sq, c4, 1.f));
+        float inv = rcp_fast(sq);
+        float C = fmaf(-dy, dy, dxe2) * inv;    // cos 2theta
+        float S = 2.f * dxe * dy * inv;         // sin 2theta
+        const float ucv = uc[3 + k];
+        if (!EED) {
+            float mu3 = sqrt_fast(mu1);
+            float hxx = (uc[2 + k] + uc[4 + k]) - 2.f * ucv;
+            float hyy = (uu[3 + k] + ud[3 + k]) - 2.f * ucv;
+            float hxy = ((ud[4 + k] + uu[2 + k]) - (ud[2 + k] + uu[4 + k])) * 0.25f;
+            float A = (hxx + hyy) * 0.5f, B = (hxx - hyy) * 0.5f;
+            float X = fmaf(C, B, S * hxy);
+            float h11 = A + X, h22 = A - X;
+            float h12 = fmaf(C, hxy, -S * B);
+            float pp = mu1 * h11, rr = mu3 * h12;
+            float hs = (pp + h22) * 0.5f, hd = (pp - h22) * 0.5f;
+            float Y = fmaf(C, hd, -S * rr);
+            o0[k] = hs + Y;                 // T_xx
+            o1[k] = fmaf(S, hd, C * rr);    // T_xy
+            o2[k] = hs - Y;                 // T_yy
+        } else {
+            float m1 = mu1 - 1.f, m2 = mu1 + 1.f;
+            float a = fmaf(C, m1, m2) * 0.5f;
+            float cc = fmaf(-C, m1, m2) * 0.5f;
+            float b = S * m1 * 0.5f;
+            o0[k] = a;
+            o1[k] = cc;
+            o2[k] = b * ((ud[3 + k] - uu[3 + k]) * 0.5f);  // b * d_y u
+            o3[k] = b * ((uc[4 + k] - uc[2 + k]) * 0.5f);  // b * d_x u
+        }
+    }
+    *reinterpret_cast<float4 *>(dst) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+    *reinterpret_cast<float4 *>(dst + PL) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+    *reinterpret_cast<float4 *>(dst + 2 * PL) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+    if (EED) *reinterpret_cast<float4 *>(dst + 3 * PL) = make_float4(o3[0], o3[1], o3[2], o3[3]);
 }
 
 template <int R, bool EED>
@@ -112,54 +180,57 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     }
     __syncthreads();
 
-    // ---- B: Gaussian x pass; out column tile-2+4q+k <- su index 4q+6+k+t ----
+    // ---- B: Gaussian x pass, 8 outputs per item; out column tile-2+8g+k <- su index 8g+6+k+t ----
     {
         float wt[2 * R + 1];
 #pragma unroll
         for (int t = 0; t <= 2 * R; ++t) wt[t] = p.wts[t];
-        constexpr int NQ = 18;  // output groups per row (columns tile-2 .. tile+69)
-        for (int i = tid; i < G::SX_H * NQ; i += 256) {
-            int q = i / G::SX_H, r = i - q * G::SX_H;  // consecutive lanes on consecutive rows
-            const float *src = su + r * G::SU_W + 4 * q;
-            float v[16];
+        constexpr int NG = 9;  // 8-wide output groups per row (columns tile-2 .. tile+69)
+        for (int i = tid; i < G::SX_H * NG; i += 256) {
+            const int g = i / G::SX_H, r = i - g * G::SX_H;  // consecutive lanes on consecutive rows
+            const float *src = su + r * G::SU_W + 8 * g;
+            float v[20];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 5; ++j) {
                 float4 a = *reinterpret_cast<const float4 *>(src + 4 * j);
                 v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
             }
-            float o[4];
+            float o[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 8; ++k) {
                 float acc = 0.f;
 #pragma unroll
                 for (int t = -R; t <= R; ++t) acc = fmaf(wt[t + R], v[6 + k + t], acc);
                 o[k] = acc;
             }
-            *reinterpret_cast<float4 *>(sx + r * G::SX_W + 4 * q) = make_float4(o[0], o[1], o[2], o[3]);
+            float *dst = sx + r * G::SX_W + 8 * g;
+            *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
         }
     }
     __syncthreads();
 
-    // ---- C: Gaussian y pass, 3 output rows per item; ss row y+2 <- sx rows y+2 .. y+2+2R ----
+    // ---- C: Gaussian y pass, 6 output rows per item; ss row y <- sx rows y .. y+2R ----
     {
         float wt[2 * R + 1];
 #pragma unroll
         for (int t = 0; t <= 2 * R; ++t) wt[t] = p.wts[t];
-        constexpr int NQ = 18;                // groups per row
-        constexpr int NS = G::SS_H / 3;       // 12 strips
-        static_assert(G::SS_H % 3 == 0, "strip height");
+        constexpr int RS = 6;              // output rows per item
+        constexpr int NQ = 17;             // groups per row (columns tile-2 .. tile+65)
+        constexpr int NS = G::SS_H / RS;   // 6 strips
+        static_assert(G::SS_H % RS == 0, "strip height");
         for (int i = tid; i < NS * NQ; i += 256) {
-            int q = i / NS, s = i - q * NS;
-            const float *src = sx + (3 * s) * G::SX_W + 4 * q;
-            float2 acc[3][2];
+            const int s = i / NQ, q = i - s * NQ;  // consecutive lanes on consecutive column groups
+            const float *src = sx + (RS * s) * G::SX_W + 4 * q;
+            float2 acc[RS][2];
 #pragma unroll
-            for (int v = 0; v < 3; ++v) acc[v][0] = acc[v][1] = make_float2(0.f, 0.f);
+            for (int v = 0; v < RS; ++v) acc[v][0] = acc[v][1] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 2 * R + 3; ++j) {
+            for (int j = 0; j < 2 * R + RS; ++j) {
                 float4 a = *reinterpret_cast<const float4 *>(src + j * G::SX_W);
                 const float2 lo = make_float2(a.x, a.y), hi = make_float2(a.z, a.w);
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
+                for (int v = 0; v < RS; ++v) {
                     const int t = j - v;  // tap index 0..2R
                     if (t >= 0 && t <= 2 * R) {
                         const float2 ww = make_float2(wt[t], wt[t]);
@@ -169,108 +240,50 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                 }
             }
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
-                *reinterpret_cast<float4 *>(ss + (3 * s + v) * G::SS_W + 4 * q) =
+            for (int v = 0; v < RS; ++v)
+                *reinterpret_cast<float4 *>(ss + (RS * s + v) * G::SS_W + 4 * q) =
                     make_float4(acc[v][0].x, acc[v][0].y, acc[v][1].x, acc[v][1].y);
         }
     }
     __syncthreads();
 
-    // ---- D: on tile+-1 (T row r <-> tile row r-1, T col 4q+k <-> tile col 4q+k-1) ----
+    // ---- D: on tile+-1 (T row r <-> tile row r-1, T col 4q+k <-> tile col 4q+k-1), two T rows
+    // per item: the three u_sigma and u rows of the first are loaded once, the second adds one of each
     constexpr int PL = G::ST_W * G::ST_H;
     {
         const float c4 = im.c4;
         constexpr int NQ = G::ST_W / 4;  // 17
-        for (int i = tid; i < G::ST_H * NQ; i += 256) {
-            int q = i / G::ST_H, r = i - q * G::ST_H;
-            // u_sigma: tile (y, x) <-> ss (y+2, x+2); this group: ss row r+1, cols 4q+1 .. 4q+4
-            const float *sm0 = ss + (r + 1) * G::SS_W + 4 * q;
-            float sc[8], sup[8], sdn[8];
-            {
-                float4 a = *reinterpret_cast<const float4 *>(sm0);
-                float4 b = *reinterpret_cast<const float4 *>(sm0 + 4);
-                sc[0] = a.x; sc[1] = a.y; sc[2] = a.z; sc[3] = a.w; sc[4] = b.x; sc[5] = b.y; sc[6] = b.z; sc[7] = b.w;
-                a = *reinterpret_cast<const float4 *>(sm0 - G::SS_W);
-                b = *reinterpret_cast<const float4 *>(sm0 - G::SS_W + 4);
-                sup[0] = a.x; sup[1] = a.y; sup[2] = a.z; sup[3] = a.w; sup[4] = b.x; sup[5] = b.y; sup[6] = b.z; sup[7] = b.w;
-                a = *reinterpret_cast<const float4 *>(sm0 + G::SS_W);
-                b = *reinterpret_cast<const float4 *>(sm0 + G::SS_W + 4);
-                sdn[0] = a.x; sdn[1] = a.y; sdn[2] = a.z; sdn[3] = a.w; sdn[4] = b.x; sdn[5] = b.y; sdn[6] = b.z; sdn[7] = b.w;
-            }
-            // u: tile (y, x) <-> su (y+HL, x+8); this group: su row r-1+HL, cols 4q+7 .. 4q+10
-            const float *um0 = su + (r - 1 + G::HL) * G::SU_W + 4 * q + 4;
-            float uc[8], uu[8], ud[8];
-            {
-                float4 a = *reinterpret_cast<const float4 *>(um0);
-                float4 b = *reinterpret_cast<const float4 *>(um0 + 4);
-                uc[0] = a.x; uc[1] = a.y; uc[2] = a.z; uc[3] = a.w; uc[4] = b.x; uc[5] = b.y; uc[6] = b.z; uc[7] = b.w;
-                a = *reinterpret_cast<const float4 *>(um0 - G::SU_W);
-                b = *reinterpret_cast<const float4 *>(um0 - G::SU_W + 4);
-                uu[0] = a.x; uu[1] = a.y; uu[2] = a.z; uu[3] = a.w; uu[4] = b.x; uu[5] = b.y; uu[6] = b.z; uu[7] = b.w;
-                a = *reinterpret_cast<const float4 *>(um0 + G::SU_W);
-                b = *reinterpret_cast<const float4 *>(um0 + G::SU_W + 4);
-                ud[0] = a.x; ud[1] = a.y; ud[2] = a.z; ud[3] = a.w; ud[4] = b.x; ud[5] = b.y; ud[6] = b.z; ud[7] = b.w;
-            }
-            float o0[4], o1[4], o2[4], o3[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                // ss index of this pixel within sc: 1+k ; su index within uc: 3+k
-                float dx = sc[2 + k] - sc[k];
-                float dy = sdn[1 + k] - sup[1 + k];
-                // A zero gradient gets v1 = (1, 0): the tiny offset leaves every
-                // representable non-negligible dx unchanged.
-                float dxe = dx + 1e-18f;
-                float dxe2 = dxe * dxe;
-                float sq = fmaf(dy, dy, dxe2);          // 4 lambda1
-                float mu1 = rsqrt_fast(fmaf(sq, c4, 1.f));
-                float inv = rcp_fast(sq);
-                float C = fmaf(-dy, dy, dxe2) * inv;    // cos 2theta
-                float S = 2.f * dxe * dy * inv;         // sin 2theta
-                const float ucv = uc[3 + k];
-                if (!EED) {
-                    float mu3 = sqrt_fast(mu1);
-                    float hxx = (uc[2 + k] + uc[4 + k]) - 2.f * ucv;
-                    float hyy = (uu[3 + k] + ud[3 + k]) - 2.f * ucv;
-                    float hxy = ((ud[4 + k] + uu[2 + k]) - (ud[2 + k] + uu[4 + k])) * 0.25f;
-                    float A = (hxx + hyy) * 0.5f, B = (hxx - hyy) * 0.5f;
-                    float X = fmaf(C, B, S * hxy);
-                    float h11 = A + X, h22 = A - X;
-                    float h12 = fmaf(C, hxy, -S * B);
-                    float pp = mu1 * h11, rr = mu3 * h12;
-                    float hs = (pp + h22) * 0.5f, hd = (pp - h22) * 0.5f;
-                    float Y = fmaf(C, hd, -S * rr);
-                    o0[k] = hs + Y;                 // T_xx
-                    o1[k] = fmaf(S, hd, C * rr);    // T_xy
-                    o2[k] = hs - Y;                 // T_yy
-                } else {
-                    float m1 = mu1 - 1.f, m2 = mu1 + 1.f;
-                    float a = fmaf(C, m1, m2) * 0.5f;
-                    float cc = fmaf(-C, m1, m2) * 0.5f;
-                    float b = S * m1 * 0.5f;
-                    o0[k] = a;
-                    o1[k] = cc;
-                    o2[k] = b * ((ud[3 + k] - uu[3 + k]) * 0.5f);  // b * d_y u
-                    o3[k] = b * ((uc[4 + k] - uc[2 + k]) * 0.5f);  // b * d_x u
-                }
-            }
-            float *dst = st + r * G::ST_W + 4 * q;
-            *reinterpret_cast<float4 *>(dst) = make_float4(o0[0], o0[1], o0[2], o0[3]);
-            *reinterpret_cast<float4 *>(dst + PL) = make_float4(o1[0], o1[1], o1[2], o1[3]);
-            *reinterpret_cast<float4 *>(dst + 2 * PL) = make_float4(o2[0], o2[1], o2[2], o2[3]);
-            if (EED) *reinterpret_cast<float4 *>(dst + 3 * PL) = make_float4(o3[0], o3[1], o3[2], o3[3]);
+        constexpr int NP = G::ST_H / 2;  // 17 row pairs
+        static_assert(G::ST_H % 2 == 0, "row pairs");
+        for (int i = tid; i < NP * NQ; i += 256) {
+            const int q = i / NP, r0 = 2 * (i - q * NP);  // consecutive lanes on consecutive row pairs
+            // T row r: u_sigma rows r .. r+2 of ss (cols 4q .. 4q+7), u rows r-2+HL .. r+HL of su (cols 4q+4 .. 4q+11)
+            const float *sm0 = ss + r0 * G::SS_W + 4 * q;
+            const float *um0 = su + (r0 - 2 + G::HL) * G::SU_W + 4 * q + 4;
+            float sa[8], sb[8], sc[8], ua[8], ub[8], uc[8];
+            ld8(sm0, sa);
+            ld8(sm0 + G::SS_W, sb);
+            ld8(sm0 + 2 * G::SS_W, sc);
+            ld8(um0, ua);
+            ld8(um0 + G::SU_W, ub);
+            ld8(um0 + 2 * G::SU_W, uc);
+            tensor_row<EED>(sa, sb, sc, ua, ub, uc, c4, st + r0 * G::ST_W + 4 * q, PL);
+            ld8(sm0 + 3 * G::SS_W, sa);
+            ld8(um0 + 3 * G::SU_W, ua);
+            tensor_row<EED>(sb, sc, sa, ub, uc, ua, c4, st + (r0 + 1) * G::ST_W + 4 * q, PL);
         }
     }
-    // Each thread owns exactly two output groups in stage E (row i/16, group i%16
-    // for i = tid, tid+256). Their u^{k-1} and mask loads are issued here, before
-    // the barrier, so that their latency overlaps the wait.
+    // Each thread owns the output groups (rows 2*(tid/16) and 2*(tid/16)+1, group
+    // tid%16) of stage E. Their u^{k-1} and mask loads are issued here, before the
+    // barrier, so that their latency overlaps the wait.
     constexpr int NQE = G::TW / 4;  // 16 groups per row
     static_assert(G::TH * NQE == 512, "two output groups per thread");
+    const int qe = tid % NQE, re = 2 * (tid / NQE);
     float4 pre_up[2];
     uint32_t pre_mk[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const int i = tid + 256 * e, r = i / NQE, q = i - r * NQE;
-        const int gy = y0 + r, gx = x0 + 4 * q;
+        const int gy = y0 + re + e, gx = x0 + 4 * qe;
         pre_up[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         pre_mk[e] = 0u;
         if (gy < h && gx < w) {
@@ -290,14 +303,16 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     }
     __syncthreads();
 
-    // ---- E: output rows tile+r, columns tile+4q .. 4q+3 (T index (r+1, 4q+1+k)) ----
+    // ---- E: output rows tile+re, tile+re+1, columns tile+4qe .. 4qe+3 (T index (r+1, 4qe+1+k)) ----
     {
-        constexpr int NQ = NQE;
+        const int q = qe;
+        // FOEED: T_xx row, T_yy rows r .. r+2 and T_xy rows r, r+2 (T rows) of output row r-1;
+        // the second output row reuses two of the T_yy rows
+        float xx[8], ya[8], yb[8], yc[8], da[8], db[8];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int i = tid + 256 * e;
-            int r = i / NQ, q = i - r * NQ;
-            int gy = y0 + r, gx = x0 + 4 * q;
+            const int r = re + e;
+            const int gy = y0 + r, gx = x0 + 4 * q;
             if (gy >= h || gx >= w) continue;
             const float *t0 = st + (r + 1) * G::ST_W + 4 * q;
             float Pu[4];
@@ -305,33 +320,27 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
             float4 ucv4 = *reinterpret_cast<const float4 *>(um);
             float ucv[4] = {ucv4.x, ucv4.y, ucv4.z, ucv4.w};
             if (!EED) {
-                float xx[8], yu[8], yc[8], yd[8], du[8], dd[8];
-                auto ld8 = [](const float *s, float *o) {
-                    float4 a = *reinterpret_cast<const float4 *>(s);
-                    float4 b = *reinterpret_cast<const float4 *>(s + 4);
-                    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-                };
+                if (e == 0) {
+                    ld8(t0 + 2 * PL - G::ST_W, ya);
+                    ld8(t0 + 2 * PL, yb);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) { ya[k] = yb[k]; yb[k] = yc[k]; }
+                }
                 ld8(t0, xx);
-                ld8(t0 + 2 * PL - G::ST_W, yu);
-                ld8(t0 + 2 * PL, yc);
-                ld8(t0 + 2 * PL + G::ST_W, yd);
-                ld8(t0 + PL - G::ST_W, du);
-                ld8(t0 + PL + G::ST_W, dd);
+                ld8(t0 + 2 * PL + G::ST_W, yc);
+                ld8(t0 + PL - G::ST_W, da);
+                ld8(t0 + PL + G::ST_W, db);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int c = 1 + k;
                     float dxx = (xx[c - 1] + xx[c + 1]) - 2.f * xx[c];
-                    float dyy = (yu[c] + yd[c]) - 2.f * yc[c];
-                    float dxy = ((dd[c + 1] + du[c - 1]) - (dd[c - 1] + du[c + 1])) * 0.5f;
+                    float dyy = (ya[c] + yc[c]) - 2.f * yb[c];
+                    float dxy = ((db[c + 1] + da[c - 1]) - (db[c - 1] + da[c + 1])) * 0.5f;
                     Pu[k] = (dxx + dyy) + dxy;
                 }
             } else {
                 float ac[8], cu[8], cc[8], cd[8], qxr[8], qyu[8], qyd[8], uu[8], ud[8], ucx[8];
-                auto ld8 = [](const float *s, float *o) {
-                    float4 a = *reinterpret_cast<const float4 *>(s);
-                    float4 b = *reinterpret_cast<const float4 *>(s + 4);
-                    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-                };
                 ld8(t0, ac);
                 ld8(t0 + PL - G::ST_W, cu);
                 ld8(t0 + PL, cc);
