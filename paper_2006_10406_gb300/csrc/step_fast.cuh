@@ -11,11 +11,14 @@
 //   B  Gaussian x pass, 8 outputs per item, columns tile-2 .. tile+69, every window row
 //   C  Gaussian y pass, 6 rows per item, columns tile-2 .. tile+65
 //   D  gradient, mu1/mu3, Hessian and T (FOEED) or the EED fluxes on tile+-1,
-//      two rows per item sharing their u_sigma and u rows
+//      segments of three (or two) rows per item sharing their u_sigma and u rows
 //   E  outer divergence, masked FSI update, optional cycle residual, float4 store;
 //      two rows per thread sharing two T_yy rows
-// The item shapes keep every warp access free of bank conflicts (odd float4
-// row strides, lanes along rows or along column groups).
+// A 128-bit shared-memory access is served in quarter-warp phases of 8 lanes,
+// each phase conflict-free only if its 8 lanes touch 8 different float4 bank
+// groups. Hence odd float4 row strides for the stages whose lanes walk down
+// rows, and lanes along 16 column groups (of the 17 a row holds) for the
+// stages whose items span several rows; the 17th group's items come last.
 // Requirements (checked on the host): row pitch a multiple of 4 elements and
 // 16-byte aligned image and mask pointers.
 #pragma once
@@ -219,8 +222,12 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         constexpr int NQ = 17;             // groups per row (columns tile-2 .. tile+65)
         constexpr int NS = G::SS_H / RS;   // 6 strips
         static_assert(G::SS_H % RS == 0, "strip height");
+        static_assert(NQ == 17, "16 column groups plus one");
         for (int i = tid; i < NS * NQ; i += 256) {
-            const int s = i / NQ, q = i - s * NQ;  // consecutive lanes on consecutive column groups
+            // lanes along the first 16 column groups of a strip (conflict-free quarter
+            // warps); the strips of the 17th group come last
+            const bool main = i < NS * 16;
+            const int s = main ? (i >> 4) : i - NS * 16, q = main ? (i & 15) : 16;
             const float *src = sx + (RS * s) * G::SX_W + 4 * q;
             float2 acc[RS][2];
 #pragma unroll
@@ -255,8 +262,15 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         constexpr int NQ = G::ST_W / 4;  // 17
         constexpr int NP = G::ST_H / 2;  // 17 row pairs
         static_assert(G::ST_H % 2 == 0, "row pairs");
-        for (int i = tid; i < NP * NQ; i += 256) {
-            const int q = i / NP, r0 = 2 * (i - q * NP);  // consecutive lanes on consecutive row pairs
+        static_assert(NQ == 17, "16 column groups plus one");
+        static_assert(G::ST_H == 34, "segments: ten of 3 rows, two of 2 rows");
+        constexpr int NSEG = 12;
+        for (int i = tid; i < NSEG * NQ; i += 256) {
+            // lanes along the first 16 column groups of a segment (conflict-free quarter
+            // warps); the segments of the 17th group come last
+            const bool main = i < NSEG * 16;
+            const int q = main ? (i & 15) : 16, sg = main ? (i >> 4) : i - NSEG * 16;
+            const int r0 = sg < 10 ? 3 * sg : 30 + 2 * (sg - 10);
             // T row r: u_sigma rows r .. r+2 of ss (cols 4q .. 4q+7), u rows r-2+HL .. r+HL of su (cols 4q+4 .. 4q+11)
             const float *sm0 = ss + r0 * G::SS_W + 4 * q;
             const float *um0 = su + (r0 - 2 + G::HL) * G::SU_W + 4 * q + 4;
@@ -271,6 +285,11 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
             ld8(sm0 + 3 * G::SS_W, sa);
             ld8(um0 + 3 * G::SU_W, ua);
             tensor_row<EED>(sb, sc, sa, ub, uc, ua, c4, st + (r0 + 1) * G::ST_W + 4 * q, PL);
+            if (sg < 10) {
+                ld8(sm0 + 4 * G::SS_W, sb);
+                ld8(um0 + 4 * G::SU_W, ub);
+                tensor_row<EED>(sc, sa, sb, uc, ua, ub, c4, st + (r0 + 2) * G::ST_W + 4 * q, PL);
+            }
         }
     }
     // Each thread owns the output groups (rows 2*(tid/16) and 2*(tid/16)+1, group
