@@ -31,17 +31,41 @@ struct AdjArgs {
     long pitch;
     T alpha, tau;
     T l2;                // lambda^2
+    T inv_l2;            // 1 / lambda^2
     T wts[2 * kRMax + 1];
     int first_of_cycle;  // 1: this step's p is u^k itself
 };
 
-constexpr int kAdjTW = 32, kAdjTH = 16;
+// Tiles of TW x 16 pixels: 64 wide in FP32, 32 wide in FP64 (shared memory).
+constexpr int kAdjTH = 16;
+template <typename T>
+constexpr int adj_tile_w() { return sizeof(T) == sizeof(float) ? 64 : 32; }
 
-// B1: P(x) v and q at every pixel of a 32 x 16 tile.
-template <typename T, int R>
+// FP32 approximations (MUFU) used by the FP32 kernels; FP64 keeps IEEE operations.
+__device__ __forceinline__ float adj_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float adj_rsqrt(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float adj_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// B1: P(x) v and q at every pixel of a TW x 16 tile.
+template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
 {
-    constexpr int TW = kAdjTW, TH = kAdjTH;
+    constexpr int TH = kAdjTH;
     constexpr int HL = R + 2;
     constexpr int XW = TW + 2 * HL, XH = TH + 2 * HL;  // x window
     constexpr int VW = TW + 4, VH = TH + 4;            // v window (tile +- 2)
@@ -92,11 +116,22 @@ __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
         const T *s0 = ss + (r + 1) * SW + (c + 1);
         const T gx = (s0[1] - s0[-1]) * T(0.5), gy = (s0[SW] - s0[-SW]) * T(0.5);
         const T rho2 = gx * gx + gy * gy;
-        const T sq = sqrt(T(1) + rho2 / l2);  // 1 / mu1
-        const T mu1 = T(1) / sq, mu3 = sqrt(mu1);
-        T C, S;
-        if (rho2 == T(0)) { C = T(1); S = T(0); }
-        else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
+        T sq, mu1, mu3, C, S;  // sq = 1 / mu1
+        if (sizeof(T) == sizeof(float)) {
+            const float t = fmaf(float(rho2), float(a.inv_l2), 1.f);
+            mu1 = adj_rsqrt(t);
+            sq = t * float(mu1);
+            mu3 = adj_sqrt(float(mu1));
+            const float inv = adj_rcp(float(rho2));
+            if (rho2 == T(0)) { C = T(1); S = T(0); }
+            else { C = (gx * gx - gy * gy) * inv; S = T(2) * gx * gy * inv; }
+        } else {
+            sq = sqrt(T(1) + rho2 / l2);
+            mu1 = T(1) / sq;
+            mu3 = sqrt(mu1);
+            if (rho2 == T(0)) { C = T(1); S = T(0); }
+            else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
+        }
         const T *x0p = sxw + (r + 1 + R) * XW + (c + 1 + R);
         const T *v0 = sv + (r + 1) * VW + (c + 1);
         const T hxx = (x0p[-1] + x0p[1]) - T(2) * x0p[0];
@@ -122,12 +157,21 @@ __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
         if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
             const int gxp = x0 + c - 1, gyp = y0 + r - 1;
             if (gxp < w && gyp < h) {
-                const T dmu1 = -mu1 * mu1 * mu1 / (T(2) * l2);  // d mu1 / d rho^2
-                const T dmu3 = dmu1 / (T(2) * mu3);
+                T dmu1, dmu3, c1, c3;  // d mu1 / d rho^2, d mu3 / d rho^2, (1 - mu1) / rho^2, (1 - mu3) / rho^2
+                if (sizeof(T) == sizeof(float)) {
+                    dmu1 = -mu1 * mu1 * mu1 * (T(0.5) * a.inv_l2);
+                    dmu3 = dmu1 * T(0.5) * adj_rsqrt(float(mu1));
+                    const float rs = adj_sqrt(float(sq));
+                    c1 = adj_rcp(float(l2 * sq * (sq + T(1))));
+                    c3 = adj_rcp(float(l2 * (sq + T(1)) * rs * (rs + T(1))));
+                } else {
+                    dmu1 = -mu1 * mu1 * mu1 / (T(2) * l2);
+                    dmu3 = dmu1 / (T(2) * mu3);
+                    const T rs = sqrt(sq);
+                    c1 = T(1) / (l2 * sq * (sq + T(1)));
+                    c3 = T(1) / (l2 * (sq + T(1)) * rs * (rs + T(1)));
+                }
                 const T srho = dmu1 * w11 * h11 + T(2) * dmu3 * w12 * h12;  // d s / d rho^2
-                const T rs = sqrt(sq);
-                const T c1 = T(1) / (l2 * sq * (sq + T(1)));             // (1 - mu1) / rho^2
-                const T c3 = T(1) / (l2 * (sq + T(1)) * rs * (rs + T(1)));  // (1 - mu3) / rho^2
                 const T th = -c1 * T(2) * (w12 * h11 + w11 * h12) - T(2) * c3 * (-(w11 - w22) * h12 - w12 * (h11 - h22));
                 const long gi = (long)gyp * pitch + gxp;
                 a.qx[gi] = T(2) * gx * srho - gy * th;
@@ -163,10 +207,10 @@ __device__ __forceinline__ T adj_divq(const AdjArgs<T> &a, int x, int y)
 }
 
 // B2: z = G (-D_odd q), then the step's adjoint recursion at every pixel of a tile.
-template <typename T, int R>
+template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
 {
-    constexpr int TW = kAdjTW, TH = kAdjTH;
+    constexpr int TH = kAdjTH;
     constexpr int RW = TW + 2 * R, RH = TH + 2 * R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sr = reinterpret_cast<T *>(smem_raw);  // -D_odd q on tile +- R (mirrored outside the image)
@@ -215,27 +259,28 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
 
 template <typename T, int R>
 struct AdjSmem {
-    static constexpr int HL = R + 2;
-    static constexpr size_t B1 = sizeof(T) * ((kAdjTW + 2 * HL) * (kAdjTH + 2 * HL) + (kAdjTW + 4) * (kAdjTH + 4) +
-                                              (kAdjTH + 2 * HL) * (kAdjTW + 4) + (kAdjTW + 4) * (kAdjTH + 4) +
-                                              3 * (kAdjTW + 2) * (kAdjTH + 2));
-    static constexpr size_t B2 = sizeof(T) * ((kAdjTW + 2 * R) * (kAdjTH + 2 * R) + (kAdjTH + 2 * R) * kAdjTW);
+    static constexpr int HL = R + 2, TW = adj_tile_w<T>(), TH = kAdjTH;
+    static constexpr size_t B1 = sizeof(T) * ((TW + 2 * HL) * (TH + 2 * HL) + (TW + 4) * (TH + 4) +
+                                              (TH + 2 * HL) * (TW + 4) + (TW + 4) * (TH + 4) + 3 * (TW + 2) * (TH + 2));
+    static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW);
 };
 
 template <typename T, int R>
 cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
 {
     using SM = AdjSmem<T, R>;
+    constexpr int TW = SM::TW, TH = SM::TH;
     if (!ap) {
-        cudaError_t e = cudaFuncSetAttribute(adj_b1_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
+        cudaError_t e =
+            cudaFuncSetAttribute(adj_b1_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(adj_b2_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
+        return cudaFuncSetAttribute(adj_b2_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
     }
-    dim3 grid((ap->w + kAdjTW - 1) / kAdjTW, (ap->h + kAdjTH - 1) / kAdjTH);
-    adj_b1_kernel<T, R><<<grid, 256, SM::B1, s>>>(*ap);
+    dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
+    adj_b1_kernel<T, R, TW><<<grid, 256, SM::B1, s>>>(*ap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_b2_kernel<T, R><<<grid, 256, SM::B2, s>>>(*ap);
+    adj_b2_kernel<T, R, TW><<<grid, 256, SM::B2, s>>>(*ap);
     return cudaGetLastError();
 }
 

@@ -742,6 +742,7 @@ foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, voi
     a.w = w; a.h = h; a.pitch = P;
     a.tau = T(tau);
     a.l2 = T(p.lambda * p.lambda);
+    a.inv_l2 = T(1.0 / (p.lambda * p.lambda));
     gauss_taps<T>(p.sigma, a.wts);
     for (int seg = V.ncp - 1; seg >= 0; --seg) {
         const long s0 = (long)seg * K, s1 = std::min<long>(S, s0 + K);
