@@ -61,39 +61,96 @@ __device__ __forceinline__ float adj_sqrt(float x)
     return r;
 }
 
+// Asynchronous global -> shared copies (cp.async) of 16 bytes, of one element, of 4 bytes.
+__device__ __forceinline__ uint32_t adj_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void adj_cp16(uint32_t d, const void *s)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(s) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void adj_cp_elem(uint32_t d, const T *s)
+{
+    if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(s) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s) : "memory");
+}
+__device__ __forceinline__ void adj_cp4(uint32_t d, const void *s)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s) : "memory");
+}
+__device__ __forceinline__ void adj_cp_wait()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 // B1: P(x) v and q at every pixel of a TW x 16 tile.
 template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
 {
     constexpr int TH = kAdjTH;
     constexpr int HL = R + 2;
-    constexpr int XW = TW + 2 * HL, XH = TH + 2 * HL;  // x window
-    constexpr int VW = TW + 4, VH = TH + 4;            // v window (tile +- 2)
-    constexpr int SW = TW + 4, SH = TH + 4;            // u_sigma on tile +- 2
-    constexpr int QW = TW + 2, QH = TH + 2;            // tile +- 1
+    constexpr int E = 16 / (int)sizeof(T);            // elements per 16 bytes
+    constexpr int XW = TW + 16, XH = TH + 2 * HL;     // x window: cols x0-8 .. x0+TW+7
+    constexpr int XOFF = 8 - HL;                      // window column of x0 - HL
+    constexpr int VW = TW + 8, VH = TH + 4;           // g and mask windows: cols x0-4 .. x0+TW+3, rows tile +- 2
+    constexpr int VOFF = 2;                           // window column of x0 - 2
+    constexpr int SW = TW + 4, SH = TH + 4;           // u_sigma on tile +- 2
+    constexpr int QW = TW + 2, QH = TH + 2;           // tile +- 1
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sxw = reinterpret_cast<T *>(smem_raw);
-    T *sv = sxw + XW * XH;
+    T *sv = sxw + XW * XH;     // g, then v = (1 - M) g
     T *sxp = sv + VW * VH;     // x pass: XH rows x SW columns
     T *ss = sxp + XH * SW;     // u_sigma
     T *tw = ss + SW * SH;      // T_w = D : H(v), 3 planes on tile +- 1
+    unsigned char *smk = reinterpret_cast<unsigned char *>(tw + 3 * QW * QH);  // mask window
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const int w = a.w, h = a.h;
     const long pitch = a.pitch;
-    for (int i = tid; i < XW * XH; i += 256) {
-        int r = i / XW, c = i - r * XW;
-        sxw[i] = a.x[(long)mirror_idx(y0 - HL + r, h) * pitch + mirror_idx(x0 - HL + c, w)];
-    }
-    for (int i = tid; i < VW * VH; i += 256) {
-        int r = i / VW, c = i - r * VW;
-        long gi = (long)mirror_idx(y0 - 2 + r, h) * pitch + mirror_idx(x0 - 2 + c, w);
-        sv[i] = a.mask[gi] ? T(0) : a.g[gi];
+    // Windows copied asynchronously: 16-byte copies where all their columns lie
+    // inside the image, otherwise element copies of the mirrored pixels.
+    {
+        const bool xin = x0 - 8 >= 0 && x0 + TW + 8 <= w;
+        const bool vin = x0 - 4 >= 0 && x0 + TW + 4 <= w;
+        const uint32_t bx = adj_smem(sxw), bv = adj_smem(sv), bm = adj_smem(smk);
+        for (int i = tid; i < XH * (XW / E); i += 256) {
+            const int r = i / (XW / E), q = i - r * (XW / E);
+            const T *row = a.x + (long)mirror_idx(y0 - HL + r, h) * pitch;
+            const int gx = x0 - 8 + E * q;
+            const uint32_t d = bx + (uint32_t)sizeof(T) * (r * XW + E * q);
+            if (xin) {
+                adj_cp16(d, row + gx);
+            } else {
+                for (int j = 0; j < E; ++j) adj_cp_elem(d + (uint32_t)sizeof(T) * j, row + mirror_idx(gx + j, w));
+            }
+        }
+        for (int i = tid; i < VH * (VW / E); i += 256) {
+            const int r = i / (VW / E), q = i - r * (VW / E);
+            const T *row = a.g + (long)mirror_idx(y0 - 2 + r, h) * pitch;
+            const int gx = x0 - 4 + E * q;
+            const uint32_t d = bv + (uint32_t)sizeof(T) * (r * VW + E * q);
+            if (vin) {
+                adj_cp16(d, row + gx);
+            } else {
+                for (int j = 0; j < E; ++j) adj_cp_elem(d + (uint32_t)sizeof(T) * j, row + mirror_idx(gx + j, w));
+            }
+        }
+        for (int i = tid; i < VH * (VW / 4); i += 256) {
+            const int r = i / (VW / 4), q = i - r * (VW / 4);
+            const uint8_t *row = a.mask + (long)mirror_idx(y0 - 2 + r, h) * pitch;
+            const int gx = x0 - 4 + 4 * q;
+            if (vin) {
+                adj_cp4(bm + (uint32_t)(r * VW + 4 * q), row + gx);
+            } else {
+                for (int j = 0; j < 4; ++j) smk[r * VW + 4 * q + j] = row[mirror_idx(gx + j, w)];
+            }
+        }
+        adj_cp_wait();
     }
     __syncthreads();
+    for (int i = tid; i < VW * VH; i += 256)  // v = (1 - M) g
+        if (smk[i]) sv[i] = T(0);
     for (int i = tid; i < XH * SW; i += 256) {  // Gaussian x pass
         int r = i / SW, c = i - r * SW;
-        const T *row = sxw + r * XW + c;
+        const T *row = sxw + r * XW + c + XOFF;
         T acc = T(0);
 #pragma unroll
         for (int t = 0; t <= 2 * R; ++t) acc += a.wts[t] * row[t];
@@ -132,8 +189,8 @@ __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
             if (rho2 == T(0)) { C = T(1); S = T(0); }
             else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
         }
-        const T *x0p = sxw + (r + 1 + R) * XW + (c + 1 + R);
-        const T *v0 = sv + (r + 1) * VW + (c + 1);
+        const T *x0p = sxw + (r + 1 + R) * XW + (c + 1 + R + XOFF);
+        const T *v0 = sv + (r + 1) * VW + (c + 1 + VOFF);
         const T hxx = (x0p[-1] + x0p[1]) - T(2) * x0p[0];
         const T hyy = (x0p[-XW] + x0p[XW]) - T(2) * x0p[0];
         const T hxy = ((x0p[XW + 1] + x0p[-XW - 1]) - (x0p[XW - 1] + x0p[-XW + 1])) * T(0.25);
@@ -260,8 +317,9 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
 template <typename T, int R>
 struct AdjSmem {
     static constexpr int HL = R + 2, TW = adj_tile_w<T>(), TH = kAdjTH;
-    static constexpr size_t B1 = sizeof(T) * ((TW + 2 * HL) * (TH + 2 * HL) + (TW + 4) * (TH + 4) +
-                                              (TH + 2 * HL) * (TW + 4) + (TW + 4) * (TH + 4) + 3 * (TW + 2) * (TH + 2));
+    static constexpr size_t B1 = sizeof(T) * ((TW + 16) * (TH + 2 * HL) + (TW + 8) * (TH + 4) +
+                                              (TH + 2 * HL) * (TW + 4) + (TW + 4) * (TH + 4) + 3 * (TW + 2) * (TH + 2)) +
+                                 (size_t)(TW + 8) * (TH + 4);
     static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW);
 };
 
