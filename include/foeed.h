@@ -87,7 +87,8 @@ typedef struct {
     float ms;               /* device time of the solve (CUDA events), milliseconds */
 } foeed_report;
 
-/* Bytes of device workspace foeed_inpaint / eed_inpaint need for a w x h image. */
+/* Bytes of device workspace foeed_inpaint / eed_inpaint need for a w x h image;
+ * 0 for an invalid size or dtype. */
 size_t foeed_workspace_bytes(int w, int h, foeed_dtype dtype);
 
 /*

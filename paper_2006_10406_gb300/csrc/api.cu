@@ -209,6 +209,21 @@ foeed_status check_image(int w, int h, long pitch, foeed_dtype d)
 
 double default_tau(bool eed, double tau) { return tau > 0.0 ? tau : (eed ? 0.25 : 0.05); }
 
+// Two timing events, destroyed on every return path.
+struct EventPair {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    cudaError_t create()
+    {
+        cudaError_t err = cudaEventCreate(&e[0]);
+        return err == cudaSuccess ? cudaEventCreate(&e[1]) : err;
+    }
+    ~EventPair()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
 struct StepCall {
     const void *uprev, *ucur, *c0;
     void *unext;
@@ -436,9 +451,9 @@ foeed_status inpaint(bool eed, const void *f, const uint8_t *mask, void *u_inout
     std::memset(&h0, 0, sizeof(h0));
     h0.tol = p.tol;
     CK(cudaMemcpyAsync(dctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    cudaEvent_t ev0, ev1;
-    CK(cudaEventCreate(&ev0));
-    CK(cudaEventCreate(&ev1));
+    EventPair evs;
+    CK(evs.create());
+    cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1];
     CK(cudaEventRecord(ev0, s));
     CK(d == FOEED_F64 ? launch_prep<double>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s)
                       : launch_prep<float>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s));
@@ -460,8 +475,6 @@ foeed_status inpaint(bool eed, const void *f, const uint8_t *mask, void *u_inout
     CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev0, ev1));
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (report) {
         report->cycles_run = hc.cycles;
         report->last_rel_change = hc.last_rel;
@@ -501,7 +514,8 @@ extern "C" {
 
 size_t foeed_workspace_bytes(int w, int h, foeed_dtype dtype)
 {
-    if (w < 1 || h < 1) return 0;
+    if (w < 1 || h < 1 || (long long)w * h > (1LL << 31) - 1) return 0;
+    if (dtype != FOEED_F32 && dtype != FOEED_F64 && dtype != FOEED_F32_F64U) return 0;
     return layout(w, h, dtype).total;
 }
 
@@ -915,16 +929,8 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     Ctl h0;
     std::memset(&h0, 0, sizeof(h0));
     h0.tol = p.tol;
-    struct Events {
-        cudaEvent_t e[2] = {nullptr, nullptr};
-        ~Events()
-        {
-            for (cudaEvent_t x : e)
-                if (x) cudaEventDestroy(x);
-        }
-    } evs;
-    CK(cudaEventCreate(&evs.e[0]));
-    CK(cudaEventCreate(&evs.e[1]));
+    EventPair evs;
+    CK(evs.create());
     cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1];
     CK(cudaEventRecord(ev0, s));
     for (int i = 0; i < count; ++i) {
