@@ -25,6 +25,9 @@
  *   - Errors are returned as foeed_status codes; nothing aborts or throws across
  *     the ABI. foeed_last_error() gives a thread-local message for the last
  *     failing call on the calling thread.
+ *   - Host threads: calls from different threads are independent (each thread
+ *     keeps its own cache of captured FSI-cycle graphs and its own capture
+ *     stream); calls that share a workspace must not overlap on the GPU.
  *   - dtype selects the storage and arithmetic type of the images: FOEED_F32
  *     (stencils in float, all reductions in double) or FOEED_F64 (double throughout).
  *     The mixed-precision FOEED_F32_F64U keeps images in float but evaluates the

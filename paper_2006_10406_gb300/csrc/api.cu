@@ -320,11 +320,14 @@ struct GraphEntry {
     unsigned long long stamp = 0;
 };
 
+// Per host thread: a graph handed out by the cache is launched after this
+// function returns, so no other thread may evict it; a thread evicts only its
+// own graphs, whose launches have completed (every solve synchronises its
+// stream before it returns).
 constexpr int kCache = 4;
-GraphEntry g_cache[kCache];
-unsigned long long g_clock = 0;
-std::mutex g_mu;
-cudaStream_t g_capture_stream[64] = {};
+thread_local GraphEntry g_cache[kCache];
+thread_local unsigned long long g_clock = 0;
+thread_local cudaStream_t g_capture_stream[64] = {};
 
 foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L,
                            char *ws, int dev, cudaGraphExec_t *out)
@@ -385,7 +388,6 @@ foeed_status get_cycle_graph(bool eed, foeed_dtype d, const foeed_params &p, int
     key.g = p.diffusivity; key.mu3 = eed ? 0 : p.mu3_mode; key.dev = dev;
     key.lambda = p.lambda; key.sigma = p.sigma; key.tau = default_tau(eed, p.tau);
     key.base = ws; key.pitch = L.P;
-    std::lock_guard<std::mutex> lk(g_mu);
     int victim = 0;
     for (int i = 0; i < kCache; ++i) {
         if (g_cache[i].exec && g_cache[i].key == key) {

@@ -438,3 +438,37 @@ def test_apply_tensor_field_with_the_foeed_tensor_is_the_foeed_operator():
     d = O.foeed_tensor_field(u, 1.0, 0.05)
     got = fg.foeed_apply_tensor_field(_dev(u, torch.float64), torch.from_numpy(d).to(DEV))
     np.testing.assert_allclose(got.cpu().numpy(), O.foeed_operator(u, 1.0, 0.05), rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# host threads: each keeps its own graph cache and capture stream
+
+def test_concurrent_solves_from_two_threads_match_sequential_solves():
+    import threading
+    img, mask, _ = synth.workload(2, h=64, w=96, instance=3)
+    f = torch.from_numpy(img.astype(np.float32)).to(DEV)
+    m = torch.from_numpy(mask).to(DEV)
+    lams = [0.01 * (i + 1) for i in range(6)]  # six graph keys per thread: the 4-entry caches evict
+    ref = {lam: fg.foeed_inpaint(f, m, lam, 1.0, 5, 3)[0].clone() for lam in lams}
+    got, errors = {}, []
+
+    def worker(tid):
+        try:
+            s = torch.cuda.Stream(device=DEV)
+            for rep in range(2):
+                for lam in (lams if tid == 0 else lams[::-1]):
+                    u, _ = fg.foeed_inpaint(f, m, lam, 1.0, 5, 3, stream=s)
+                    got[(tid, rep, lam)] = u
+            torch.cuda.synchronize(DEV)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    ts = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    assert len(got) == 2 * 2 * len(lams)
+    for (tid, rep, lam), u in got.items():
+        assert torch.equal(u, ref[lam]), (tid, rep, lam)
