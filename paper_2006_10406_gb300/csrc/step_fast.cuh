@@ -328,6 +328,8 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         // FOEED: T_xx row, T_yy rows r .. r+2 and T_xy rows r, r+2 (T rows) of output row r-1;
         // the second output row reuses two of the T_yy rows
         float xx[8], ya[8], yb[8], yc[8], da[8], db[8];
+        // EED: plane-1 rows r .. r+2 (the second output row reuses two) and the u rows
+        float cu[8], cc[8], cd[8], ud4[4], uc4[4];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int r = re + e;
@@ -336,8 +338,14 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
             const float *t0 = st + (r + 1) * G::ST_W + 4 * q;
             float Pu[4];
             const float *um = su + (r + G::HL) * G::SU_W + 4 * q + 8;  // u^k at this group
-            float4 ucv4 = *reinterpret_cast<const float4 *>(um);
-            float ucv[4] = {ucv4.x, ucv4.y, ucv4.z, ucv4.w};
+            float ucv[4];
+            if (EED && e == 1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ucv[k] = ud4[k];
+            } else {
+                const float4 ucv4 = *reinterpret_cast<const float4 *>(um);
+                ucv[0] = ucv4.x; ucv[1] = ucv4.y; ucv[2] = ucv4.z; ucv[3] = ucv4.w;
+            }
             if (!EED) {
                 if (e == 0) {
                     ld8(t0 + 2 * PL - G::ST_W, ya);
@@ -359,10 +367,15 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                     Pu[k] = (dxx + dyy) + dxy;
                 }
             } else {
-                float ac[8], cu[8], cc[8], cd[8], qxr[8], qyu[8], qyd[8], uu[8], ud[8], ucx[8];
+                float ac[8], qxr[8], qyu[8], qyd[8], uu[4], ud[4], ucx[8];
                 ld8(t0, ac);
-                ld8(t0 + PL - G::ST_W, cu);
-                ld8(t0 + PL, cc);
+                if (e == 0) {
+                    ld8(t0 + PL - G::ST_W, cu);
+                    ld8(t0 + PL, cc);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) { cu[k] = cc[k]; cc[k] = cd[k]; }
+                }
                 ld8(t0 + PL + G::ST_W, cd);
                 ld8(t0 + 2 * PL, qxr);
                 ld8(t0 + 3 * PL - G::ST_W, qyu);
@@ -370,12 +383,19 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                 // u neighbours: su cols 4q+7 .. 4q+12 <-> ucx[3..8]; load su cols 4q+4 .. 4q+11 and 4q+12
                 ld8(um - 4, ucx);
                 float ur = um[4];
-                {
-                    float4 a = *reinterpret_cast<const float4 *>(um - G::SU_W);
+                if (e == 0) {
+                    const float4 a = *reinterpret_cast<const float4 *>(um - G::SU_W);
                     uu[0] = a.x; uu[1] = a.y; uu[2] = a.z; uu[3] = a.w;
-                    a = *reinterpret_cast<const float4 *>(um + G::SU_W);
+                } else {  // the row above is the first output row's own
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) uu[k] = uc4[k];
+                }
+                {
+                    const float4 a = *reinterpret_cast<const float4 *>(um + G::SU_W);
                     ud[0] = a.x; ud[1] = a.y; ud[2] = a.z; ud[3] = a.w;
                 }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { uc4[k] = ucv[k]; ud4[k] = ud[k]; }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int c = 1 + k;
