@@ -39,8 +39,8 @@ WORKLOAD = 3
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel on the full 2048x2048 workload, and the hash of the
 # kernel source it was taken on; reported only while the source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "f556a6feff95de98d200c9cce30fc4569a721abf",
-               "bytes_per_launch": 37796352 + 19456}  # profiles/fsi_step_fast_foeed_f32_r5_2048x2048.md
+NCU_TRAFFIC = {"source_sha1": "042c0019e9bc2b4cac4f0c9fe7b0ff5c9446c6eb",
+               "bytes_per_launch": 37796352 + 15360}  # profiles/fsi_step_fast_foeed_f32_r5_2048x2048.md
 
 
 def kernel_source_sha1():
@@ -232,6 +232,29 @@ def batched_leg(fg, synth, torch, dev, stream):
             "max_abs_diff_vs_one_by_one": diff, "fsi_cycles": cycles, "cycle_len": n}
 
 
+def convergence_leg(fg, synth, torch, dev, stream):
+    """W2 (512 x 512 polygons, 4% mask): FOEED and EED solved until the relative
+    change of a cycle falls below 1e-6 (at most 20000 cycles), FP32."""
+    import numpy as np
+    img, mask, p = synth.workload(2)
+    f = torch.from_numpy(img.astype(np.float32)).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    imgd = torch.from_numpy(img).to(dev)
+    out = {}
+    for name, solve in (("foeed", fg.foeed_inpaint), ("eed", fg.eed_inpaint)):
+        solve(f, m, p["lam"], p["sigma"], p["cycle_len"], 2, stream=stream)  # capture
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        u, rep = solve(f, m, p["lam"], p["sigma"], p["cycle_len"], p["max_cycles"], tol=p["tol"], stream=stream,
+                       raise_on_status=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        mse, aae, psnr = fg.foeed_errors(u.double(), imgd)
+        out[name] = {"converged": rep.converged, "cycles": rep.cycles_run, "last_rel_change": rep.last_rel_change,
+                     "ms": a.elapsed_time(b), "psnr_db": psnr, "mse": mse}
+    return {"workload": p["name"], "tol": p["tol"], "cycle_len": p["cycle_len"], **out}
+
+
 def adjoint_leg(fg, synth, torch, dev, stream):
     """W5 tonal optimisation: 1024 x 1024 FP32, 4% mask, 30 FSI cycles of length 20
     unrolled; 20 Adam steps on the stored grey values with the gradient of the
@@ -263,7 +286,18 @@ def adjoint_leg(fg, synth, torch, dev, stream):
             with torch.no_grad():
                 f.clamp_(0.0, 1.0)
     steps = n * cycles
-    return {"iterations": 20, "mse_start": mse[0], "mse_end": mse[-1],
+    # one gradient alone, checkpoint every 16 steps (recomputed segments) and every step (all states kept)
+    grad_ms = {}
+    g = torch.ones_like(target) * 1e-3
+    for k in (16, 1):
+        fg.foeed_inpaint_vjp(target, md, g, p["lam"], p["sigma"], n, cycles, checkpoint_every=k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fg.foeed_inpaint_vjp(target, md, g, p["lam"], p["sigma"], n, cycles, checkpoint_every=k)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        grad_ms[f"checkpoint_every_{k}"] = a.elapsed_time(b)
+    return {"iterations": 20, "mse_start": mse[0], "mse_end": mse[-1], "gradient_ms": grad_ms,
             "mse_drop_pct": 100.0 * (mse[0] - mse[-1]) / mse[0],
             "psnr_start_db": float(10 * np.log10(1.0 / mse[0])), "psnr_end_db": float(10 * np.log10(1.0 / mse[-1])),
             "ms_per_iteration": float(np.median(ev)), "unrolled_steps": steps, "checkpoint_every": 16,
@@ -295,6 +329,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-convergence", action="store_true")
     ap.add_argument("--minimal", action="store_true",
                     help="only the warm-up and timed solves (for profiler launch lists)")
     args = ap.parse_args()
@@ -457,6 +492,8 @@ def main():
         extra["batched"] = batched_leg(fg, synth, torch, dev, stream)
     if rank == 0 and not args.no_adjoint:
         extra["adjoint"] = adjoint_leg(fg, synth, torch, dev, stream)
+    if rank == 0 and not args.no_convergence:
+        extra["convergence"] = convergence_leg(fg, synth, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
