@@ -86,7 +86,9 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
             float X = fmaf(C, B, S * hxy);
             float h11 = A + X, h22 = A - X;
             float h12 = fmaf(C, hxy, -S * B);
-            float pp = mu1 * h11, rr = mu3 * h12;
+            // rounded products (no contraction into the sums below): the same bits in every
+            // instantiation of the kernel
+            float pp = __fmul_rn(mu1, h11), rr = mu3 * h12;
             float hs = (pp + h22) * 0.5f, hd = (pp - h22) * 0.5f;
             float Y = fmaf(C, hd, -S * rr);
             o0[k] = hs + Y;                 // T_xx
@@ -109,9 +111,12 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
     if (EED) *reinterpret_cast<float4 *>(dst + 3 * PL) = make_float4(o3[0], o3[1], o3[2], o3[3]);
 }
 
-template <int R, bool EED>
+// Tile geometry: 64 x TH output pixels, TH = 32 (large images) or 16 (images
+// with fewer tiles than the GPU has SMs: more, shorter CTAs per step).
+template <int R, bool EED, int TH_ = 32>
 struct FastTile {
-    static constexpr int TW = 64, TH = 32;
+    static constexpr int TW = 64, TH = TH_;
+    static_assert(TH == 32 || TH == 16, "tile height");
     static constexpr int HL = R + 2;
     static constexpr int SU_W = 84, SU_H = TH + 2 * HL;  // u: columns tile-8 .. tile+75
     // Row strides are an odd number of float4 so that the column-major stages
@@ -124,6 +129,13 @@ struct FastTile {
     static constexpr int SXT = (SX_W * SX_H > NT * ST_W * ST_H) ? SX_W * SX_H : NT * ST_W * ST_H;
     static constexpr int ELEMS = SU_W * SU_H + SXT + SS_W * SS_H;
     static constexpr size_t SMEM = sizeof(float) * ELEMS;
+    // y pass: strips of RS rows; tensor stage: N3 segments of 3 rows, then N2 of 2
+    static constexpr int RS = SS_H % 6 == 0 ? 6 : 5;
+    static_assert(SS_H % RS == 0, "strip height");
+    static constexpr int N2 = ST_H % 3 == 0 ? 0 : (ST_H % 3 == 1 ? 2 : 1);
+    static constexpr int N3 = (ST_H - 2 * N2) / 3;
+    // output stage: ER rows per thread (16 four-pixel groups per row, 256 threads)
+    static constexpr int ER = TH * (TW / 4) / 256;
 };
 
 // The image one tile belongs to: its buffers for this step and its geometry.
@@ -137,14 +149,14 @@ struct TileImg {
     float c4;             // 1/(4 lambda^2)
 };
 
-// One 64 x 32 tile of one FSI step (stages A..E) of image im; p supplies the
+// One 64 x TH tile of one FSI step (stages A..E) of image im; p supplies the
 // Gaussian taps, alpha, tau and whether this step accumulates the cycle
 // residual (added to rnum/rden).
-template <int R, bool EED, typename U>
+template <int R, bool EED, typename U, int TH = 32>
 __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileImg &im, const int x0, const int y0,
                                           float *sm, double &rnum, double &rden)
 {
-    using G = FastTile<R, EED>;
+    using G = FastTile<R, EED, TH>;
     float *su = sm;
     float *sx = su + G::SU_W * G::SU_H;
     float *st = sx;  // aliases sx: written in stage D, after the last read of sx in stage C
@@ -213,15 +225,14 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     }
     __syncthreads();
 
-    // ---- C: Gaussian y pass, 6 output rows per item; ss row y <- sx rows y .. y+2R ----
+    // ---- C: Gaussian y pass, RS output rows per item; ss row y <- sx rows y .. y+2R ----
     {
         float wt[2 * R + 1];
 #pragma unroll
         for (int t = 0; t <= 2 * R; ++t) wt[t] = p.wts[t];
-        constexpr int RS = 6;              // output rows per item
+        constexpr int RS = G::RS;          // output rows per item
         constexpr int NQ = 17;             // groups per row (columns tile-2 .. tile+65)
-        constexpr int NS = G::SS_H / RS;   // 6 strips
-        static_assert(G::SS_H % RS == 0, "strip height");
+        constexpr int NS = G::SS_H / RS;   // strips
         static_assert(NQ == 17, "16 column groups plus one");
         for (int i = tid; i < NS * NQ; i += 256) {
             // lanes along the first 16 column groups of a strip (conflict-free quarter
@@ -260,17 +271,14 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     {
         const float c4 = im.c4;
         constexpr int NQ = G::ST_W / 4;  // 17
-        constexpr int NP = G::ST_H / 2;  // 17 row pairs
-        static_assert(G::ST_H % 2 == 0, "row pairs");
         static_assert(NQ == 17, "16 column groups plus one");
-        static_assert(G::ST_H == 34, "segments: ten of 3 rows, two of 2 rows");
-        constexpr int NSEG = 12;
+        constexpr int NSEG = G::N3 + G::N2;  // TH 32: ten segments of 3 rows, two of 2; TH 16: six of 3
         for (int i = tid; i < NSEG * NQ; i += 256) {
             // lanes along the first 16 column groups of a segment (conflict-free quarter
             // warps); the segments of the 17th group come last
             const bool main = i < NSEG * 16;
             const int q = main ? (i & 15) : 16, sg = main ? (i >> 4) : i - NSEG * 16;
-            const int r0 = sg < 10 ? 3 * sg : 30 + 2 * (sg - 10);
+            const int r0 = sg < G::N3 ? 3 * sg : 3 * G::N3 + 2 * (sg - G::N3);
             // T row r: u_sigma rows r .. r+2 of ss (cols 4q .. 4q+7), u rows r-2+HL .. r+HL of su (cols 4q+4 .. 4q+11)
             const float *sm0 = ss + r0 * G::SS_W + 4 * q;
             const float *um0 = su + (r0 - 2 + G::HL) * G::SU_W + 4 * q + 4;
@@ -285,23 +293,24 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
             ld8(sm0 + 3 * G::SS_W, sa);
             ld8(um0 + 3 * G::SU_W, ua);
             tensor_row<EED>(sb, sc, sa, ub, uc, ua, c4, st + (r0 + 1) * G::ST_W + 4 * q, PL);
-            if (sg < 10) {
+            if (sg < G::N3) {
                 ld8(sm0 + 4 * G::SS_W, sb);
                 ld8(um0 + 4 * G::SU_W, ub);
                 tensor_row<EED>(sc, sa, sb, uc, ua, ub, c4, st + (r0 + 2) * G::ST_W + 4 * q, PL);
             }
         }
     }
-    // Each thread owns the output groups (rows 2*(tid/16) and 2*(tid/16)+1, group
+    // Each thread owns the output groups (rows ER*(tid/16) .. ER*(tid/16)+ER-1, group
     // tid%16) of stage E. Their u^{k-1} and mask loads are issued here, before the
     // barrier, so that their latency overlaps the wait.
     constexpr int NQE = G::TW / 4;  // 16 groups per row
-    static_assert(G::TH * NQE == 512, "two output groups per thread");
-    const int qe = tid % NQE, re = 2 * (tid / NQE);
-    float4 pre_up[2];
-    uint32_t pre_mk[2];
+    constexpr int ER = G::ER;       // rows per thread
+    static_assert(G::TH * NQE == 256 * ER, "whole output groups per thread");
+    const int qe = tid % NQE, re = ER * (tid / NQE);
+    float4 pre_up[ER];
+    uint32_t pre_mk[ER];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < ER; ++e) {
         const int gy = y0 + re + e, gx = x0 + 4 * qe;
         pre_up[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         pre_mk[e] = 0u;
@@ -322,7 +331,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     }
     __syncthreads();
 
-    // ---- E: output rows tile+re, tile+re+1, columns tile+4qe .. 4qe+3 (T index (r+1, 4qe+1+k)) ----
+    // ---- E: output rows tile+re .. tile+re+ER-1, columns tile+4qe .. 4qe+3 (T index (r+1, 4qe+1+k)) ----
     {
         const int q = qe;
         // FOEED: T_xx row, T_yy rows r .. r+2 and T_xy rows r, r+2 (T rows) of output row r-1;
@@ -331,7 +340,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         // EED: plane-1 rows r .. r+2 (the second output row reuses two) and the u rows
         float cu[8], cc[8], cd[8], ud4[4], uc4[4];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
+        for (int e = 0; e < ER; ++e) {
             const int r = re + e;
             const int gy = y0 + r, gx = x0 + 4 * q;
             if (gy >= h || gx >= w) continue;
@@ -402,8 +411,9 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                     float u0 = ucv[k];
                     float ul = ucx[3 + k];
                     float urr = (k == 3) ? ur : ucx[5 + k];
-                    float fx = ((ac[c] + ac[c + 1]) * (urr - u0) - (ac[c - 1] + ac[c]) * (u0 - ul)) * 0.5f;
-                    float fy = ((cc[c] + cd[c]) * (ud[k] - u0) - (cu[c] + cc[c]) * (u0 - uu[k])) * 0.5f;
+                    // the fluxes as explicit fma(a, b, -round(c d)): the same bits in every instantiation
+                    float fx = fmaf(ac[c] + ac[c + 1], urr - u0, -__fmul_rn(ac[c - 1] + ac[c], u0 - ul)) * 0.5f;
+                    float fy = fmaf(cc[c] + cd[c], ud[k] - u0, -__fmul_rn(cu[c] + cc[c], u0 - uu[k])) * 0.5f;
                     // plane 2 holds b * d_y u (differentiated in x), plane 3 b * d_x u (in y)
                     float mx = qxr[c + 1] - qxr[c - 1];
                     float my = qyd[c] - qyu[c];
@@ -430,8 +440,8 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                     un[k] = ucv[k];
                 } else {
                     U up = U(upv[k]);
-                    U ex = U(ucv[k]) - tau * U(Pu[k]);
-                    un[k] = float(up + alpha * (ex - up));
+                    const U ex = fma(-tau, U(Pu[k]), U(ucv[k]));  // u^k - tau P u^k
+                    un[k] = float(fma(alpha, ex - up, up));
                 }
             }
             if (p.residual) {
@@ -471,8 +481,12 @@ __device__ __forceinline__ void finish_cycle_residual(double rnum, double rden, 
     }
 }
 
-// One FSI step over one image, one CTA per 64 x 32 tile.
-template <int R, bool EED, typename U>
+// Images with fewer 64 x 32 tiles than this run on 64 x 16 tiles: they fill
+// less than a wave of the GPU, and a step's time is the latency of one tile.
+constexpr long long kFastSmallTiles = 304;
+
+// One FSI step over one image, one CTA per 64 x TH tile.
+template <int R, bool EED, typename U, int TH>
 __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
 {
     extern __shared__ __align__(16) float sm[];
@@ -485,7 +499,7 @@ __global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const TileImg im{p.uprev, p.ucur, p.unext, p.mask, p.c0, p.w, p.h, p.pitch, p.c4};
     double rnum = 0.0, rden = 0.0;
-    fast_tile<R, EED, U>(p, im, blockIdx.x * FastTile<R, EED>::TW, blockIdx.y * FastTile<R, EED>::TH, sm, rnum, rden);
+    fast_tile<R, EED, U, TH>(p, im, blockIdx.x * FastTile<R, EED, TH>::TW, blockIdx.y * TH, sm, rnum, rden);
     if (p.residual)
         finish_cycle_residual(rnum, rden, p.ctl, p.partials, gridDim.x * gridDim.y,
                               blockIdx.y * gridDim.x + blockIdx.x, red);
@@ -550,11 +564,22 @@ cudaError_t launch_fsi_batch_step_fast(const StepArgs<float> *ap, const BatchArg
 template <int R, bool EED, typename U>
 cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
 {
-    using G = FastTile<R, EED>;
-    auto kern = fsi_step_fast<R, EED, U>;
-    if (!ap) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    dim3 grid((ap->w + G::TW - 1) / G::TW, (ap->h + G::TH - 1) / G::TH);
-    return launch_step_kernel(kern, grid, 256, G::SMEM, s, *ap);
+    using G32 = FastTile<R, EED, 32>;
+    using G16 = FastTile<R, EED, 16>;
+    auto k32 = fsi_step_fast<R, EED, U, 32>;
+    auto k16 = fsi_step_fast<R, EED, U, 16>;
+    if (!ap) {
+        cudaError_t e = cudaFuncSetAttribute(k32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G32::SMEM);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G16::SMEM);
+    }
+    const int ntx = (ap->w + 63) / 64;
+    if ((long long)ntx * ((ap->h + 31) / 32) < kFastSmallTiles) {
+        dim3 grid(ntx, (ap->h + 15) / 16);
+        return launch_step_kernel(k16, grid, 256, G16::SMEM, s, *ap);
+    }
+    dim3 grid(ntx, (ap->h + 31) / 32);
+    return launch_step_kernel(k32, grid, 256, G32::SMEM, s, *ap);
 }
 
 }  // namespace foeed

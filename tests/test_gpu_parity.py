@@ -350,7 +350,9 @@ def test_batch_equals_single_image_solves(n, dtype):
         ref, rr = fg.foeed_inpaint(f, m, lam, 1.0, n, 4, dtype=dtype)
         assert r.cycles_run == rr.cycles_run == 4
         assert torch.equal(u, ref), float((u - ref).abs().max())
-        assert r.last_rel_change == rr.last_rel_change
+        # the images are bitwise equal; the residual is an FP64 sum over tiles, and a small
+        # single image runs on 64 x 16 tiles where the batch uses 64 x 32
+        assert r.last_rel_change == pytest.approx(rr.last_rel_change, rel=1e-12, abs=0)
 
 
 def test_batch_matches_oracle_and_keeps_known_pixels():
@@ -389,7 +391,9 @@ def test_eed_batch_equals_single_image_solves(n):
     for f, m, lam, u, r in zip(imgs, masks, lams, outs, reps):
         ref, rr = fg.eed_inpaint(f, m, lam, 1.0, n, 3)
         assert torch.equal(u, ref), float((u - ref).abs().max())
-        assert r.last_rel_change == rr.last_rel_change
+        # the images are bitwise equal; the residual is an FP64 sum over tiles, and a small
+        # single image runs on 64 x 16 tiles where the batch uses 64 x 32
+        assert r.last_rel_change == pytest.approx(rr.last_rel_change, rel=1e-12, abs=0)
 
 
 def test_eed_batch_matches_oracle():
