@@ -292,7 +292,9 @@ def _pitched(a, pitch, dtype):
 
 
 @pytest.mark.parametrize("method", [0, 1])
-@pytest.mark.parametrize("shape", [(100, 130), (33, 70), (64, 64), (5, 300), (130, 7)])
+# the small shapes run the fast kernel on 64 x 16 tiles; 630 x 1030 (340 tiles of
+# 64 x 32, ragged in both directions) on 64 x 32 tiles
+@pytest.mark.parametrize("shape", [(100, 130), (33, 70), (64, 64), (5, 300), (130, 7), (630, 1030)])
 @pytest.mark.parametrize("sigma", [0.5, 1.0, 1.5, 2.0])
 def test_fast_and_generic_f32_paths_match_oracle(method, shape, sigma):
     rng = _rng(200 + method)
