@@ -255,6 +255,26 @@ def convergence_leg(fg, synth, torch, dev, stream):
     return {"workload": p["name"], "tol": p["tol"], "cycle_len": p["cycle_len"], **out}
 
 
+def gradient_once(fg, synth, torch, dev, rank):
+    """One warm-up and one timed gradient of the W5 workload (checkpoint every 16 steps)."""
+    import numpy as np
+    img, mask, p = synth.workload(5)
+    f = torch.from_numpy(img.astype(np.float32)).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    g = torch.full_like(f, 1e-3)
+    args = (f, m, g, p["lam"], p["sigma"], p["cycle_len"], p["max_cycles"])
+    fg.foeed_inpaint_vjp(*args, checkpoint_every=16)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    gf, _ = fg.foeed_inpaint_vjp(*args, checkpoint_every=16)
+    b.record()
+    torch.cuda.synchronize(dev)
+    if rank == 0:
+        print(json.dumps({"gradient_ms": a.elapsed_time(b), "workload": p["name"],
+                          "grad_norm": float(gf.norm())}), flush=True)
+
+
 def adjoint_leg(fg, synth, torch, dev, stream):
     """W5 tonal optimisation: 1024 x 1024 FP32, 4% mask, 30 FSI cycles of length 20
     unrolled; 20 Adam steps on the stored grey values with the gradient of the
@@ -332,6 +352,9 @@ def main():
     ap.add_argument("--no-convergence", action="store_true")
     ap.add_argument("--minimal", action="store_true",
                     help="only the warm-up and timed solves (for profiler launch lists)")
+    ap.add_argument("--gradient-only", action="store_true",
+                    help="only one warm-up and one timed gradient of the 1024^2 tonal-optimisation "
+                         "workload (for profiler launch lists of the backward kernels)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -346,6 +369,8 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.gradient_only:
+        return gradient_once(fg, synth, torch, dev, rank)
     pg = None
     if world > 1:
         import torch.distributed as dist
