@@ -6,6 +6,7 @@ conservation, Dirichlet pixels, equivariance), library routines (numpy eigh,
 numpy linear solve) or a dense brute-force assembly with explicit transposes.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -91,6 +92,57 @@ def test_other_diffusivities_closed_forms():
     assert abs(O.diffusivity(O.G_PERONA_MALIK2, lam ** 2, lam) - math.exp(-1)) < 1e-15
     assert abs(O.diffusivity(O.G_GEMAN_REYNOLDS, 0.0, lam) - 2 / lam ** 2) < 1e-9
     assert O.diffusivity(O.G_AUBERT, 0.0, lam) == 0.0
+
+
+def _table6_rows():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table6_diffusivities.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if line:
+                rows.append((int(line[0]), float(line[1]), float(line[2]), float(line[3])))
+    return rows
+
+
+@pytest.mark.parametrize("kind,ratio,lam,expected", _table6_rows())
+def test_table6_diffusivities_at_hand_computed_points(kind, ratio, lam, expected):
+    """Each Table 6 diffusivity at s = lambda/2, lambda, 3 lambda for two lambdas,
+    against values worked out by hand from the printed formulas (tests/golden)."""
+    s = ratio * lam
+    got = O.diffusivity(kind, s * s, lam)
+    assert abs(got - expected) <= 1e-13 * max(1.0, abs(expected)), (kind, ratio, lam, got, expected)
+
+
+@pytest.mark.parametrize("kind", [O.G_CHARBONNIER, O.G_PERONA_MALIK, O.G_PERONA_MALIK2, O.G_GEMAN_REYNOLDS])
+def test_table6_decreasing_diffusivities_are_monotone(kind):
+    lam = 0.07
+    s = np.linspace(0.0, 5 * lam, 200)
+    g = np.array([O.diffusivity(kind, v * v, lam) for v in s])
+    assert np.all(np.diff(g) < 0)
+
+
+def test_aubert_rises_to_its_maximum_at_s_equal_lambda_then_falls():
+    """(s/l)^2/(s^2+l^2)^2 as a function of t = s^2 is t/(l^2 (t+l^2)^2), whose
+    derivative vanishes at t = l^2 only: increasing below s = lambda, decreasing above."""
+    lam = 0.07
+    below = np.linspace(0.0, lam, 100)
+    above = np.linspace(lam, 5 * lam, 100)
+    gb = np.array([O.diffusivity(O.G_AUBERT, v * v, lam) for v in below])
+    ga = np.array([O.diffusivity(O.G_AUBERT, v * v, lam) for v in above])
+    assert np.all(np.diff(gb) > 0) and np.all(np.diff(ga) < 0)
+    assert abs(ga[0] - 1.0 / (4 * lam ** 4)) < 1e-9 / lam ** 4
+
+
+def test_table6_scaling_in_lambda():
+    """At a fixed ratio s/lambda, Charbonnier and both Perona-Malik forms do not depend
+    on lambda, Geman-Reynolds scales as lambda^-2 and Aubert as lambda^-4."""
+    for r in (0.3, 1.7):
+        for kind, p in ((O.G_CHARBONNIER, 0), (O.G_PERONA_MALIK, 0), (O.G_PERONA_MALIK2, 0),
+                        (O.G_GEMAN_REYNOLDS, 2), (O.G_AUBERT, 4)):
+            a = O.diffusivity(kind, (r * 0.1) ** 2, 0.1)
+            b = O.diffusivity(kind, (r * 0.05) ** 2, 0.05)
+            assert abs(b / a - 2.0 ** p) < 1e-12 * 2.0 ** p, (kind, r, a, b)
 
 
 # --------------------------------------------------------------------------
