@@ -65,36 +65,45 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
     float o0[4], o1[4], o2[4], o3[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float dx = sc[2 + k] - sc[k];
-        float dy = sdn[1 + k] - sup[1 + k];
-        // A zero gradient gets v1 = (1, 0): the tiny offset leaves every
-        // representable non-negligible dx unchanged.
-        float dxe = dx + 1e-18f;
-        float dxe2 = dxe * dxe;
-        float sq = fmaf(dy, dy, dxe2);          // 4 lambda1
-        float mu1 = rsqrt_fast(fmaf(sq, c4, 1.f));
-        float inv = rcp_fast(sq);
-        float C = fmaf(-dy, dy, dxe2) * inv;    // cos 2theta
-        float S = 2.f * dxe * dy * inv;         // sin 2theta
+        const float dx = __fsub_rn(sc[2 + k], sc[k]);
+        const float dy = __fsub_rn(sdn[1 + k], sup[1 + k]);
         const float ucv = uc[3 + k];
         if (!EED) {
-            float mu3 = sqrt_fast(mu1);
-            float hxx = (uc[2 + k] + uc[4 + k]) - 2.f * ucv;
-            float hyy = (uu[3 + k] + ud[3 + k]) - 2.f * ucv;
-            float hxy = ((ud[4 + k] + uu[2 + k]) - (ud[2 + k] + uu[4 + k])) * 0.25f;
-            float A = (hxx + hyy) * 0.5f, B = (hxx - hyy) * 0.5f;
-            float X = fmaf(C, B, S * hxy);
-            float h11 = A + X, h22 = A - X;
-            float h12 = fmaf(C, hxy, -S * B);
-            // rounded products (no contraction into the sums below): the same bits in every
-            // instantiation of the kernel
-            float pp = __fmul_rn(mu1, h11), rr = mu3 * h12;
-            float hs = (pp + h22) * 0.5f, hd = (pp - h22) * 0.5f;
-            float Y = fmaf(C, hd, -S * rr);
-            o0[k] = hs + Y;                 // T_xx
-            o1[k] = fmaf(S, hd, C * rr);    // T_xy
-            o2[k] = hs - Y;                 // T_yy
+            // the offset keeps 1/s2^2 finite for a zero gradient (where mu1 = mu3 = 1
+            // and the corrections vanish); it is below the rounding of any dy^2 > 1e-11
+            const float qq = __fmaf_rn(dy, dy, 1e-18f);
+            const float pp = __fmul_rn(dx, dx);
+            const float pq = __fmul_rn(dx, dy);
+            const float s2 = __fadd_rn(pp, qq);
+            const float mu1 = rsqrt_fast(__fmaf_rn(s2, c4, 1.f));
+            const float inv = rcp_fast(s2);
+            const float inv2 = __fmul_rn(inv, inv);
+            const float k1 = __fmaf_rn(mu1, inv2, -inv2);  // (mu1 - 1) / s2^2
+            const float mu3 = sqrt_fast(mu1);
+            const float k3n = __fmaf_rn(-mu3, inv2, inv2);  // (1 - mu3) / s2^2
+            const float hxx = __fmaf_rn(-2.f, ucv, __fadd_rn(uc[2 + k], uc[4 + k]));
+            const float hyy = __fmaf_rn(-2.f, ucv, __fadd_rn(uu[3 + k], ud[3 + k]));
+            const float hxy =
+                __fmul_rn(__fsub_rn(__fadd_rn(ud[4 + k], uu[2 + k]), __fadd_rn(ud[2 + k], uu[4 + k])), 0.25f);
+            const float d = __fsub_rn(pp, qq);
+            const float pq2 = __fadd_rn(pq, pq);
+            const float e1 = __fmaf_rn(pq2, hxy, __fmaf_rn(pp, hxx, __fmul_rn(qq, hyy)));  // g^T H g
+            const float e3 = __fmaf_rn(pq, __fsub_rn(hyy, hxx), __fmul_rn(d, hxy));         // g^T H g_perp
+            const float a = __fmul_rn(k1, e1);
+            const float bn = __fmul_rn(k3n, e3);
+            o0[k] = __fmaf_rn(a, pp, __fmaf_rn(bn, pq2, hxx));   // T_xx
+            o1[k] = __fmaf_rn(a, pq, __fmaf_rn(-bn, d, hxy));    // T_xy
+            o2[k] = __fmaf_rn(a, qq, __fmaf_rn(-bn, pq2, hyy));  // T_yy
         } else {
+            // A zero gradient gets v1 = (1, 0): the tiny offset leaves every
+            // representable non-negligible dx unchanged.
+            float dxe = dx + 1e-18f;
+            float dxe2 = dxe * dxe;
+            float sq = fmaf(dy, dy, dxe2);          // 4 lambda1
+            float mu1 = rsqrt_fast(fmaf(sq, c4, 1.f));
+            float inv = rcp_fast(sq);
+            float C = fmaf(-dy, dy, dxe2) * inv;    // cos 2theta
+            float S = 2.f * dxe * dy * inv;         // sin 2theta
             float m1 = mu1 - 1.f, m2 = mu1 + 1.f;
             float a = fmaf(C, m1, m2) * 0.5f;
             float cc = fmaf(-C, m1, m2) * 0.5f;
@@ -168,27 +177,42 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     const int w = im.w, h = im.h;
     const long pitch = im.pitch;
 
-    // ---- A: u window, copied global -> shared asynchronously (cp.async) ----
+    // ---- A: u window, copied global -> shared asynchronously (cp.async). Thread tid < 252
+    // owns the float4 column q = tid % 21 and the rows r0 = tid / 21, r0 + 12, ...; interior
+    // tiles copy 16 bytes per row with no index arithmetic beyond a pointer increment ----
     {
         const float *__restrict__ uc = im.ucur;
         const bool xin = (x0 - 8 >= 0) && (x0 + 76 <= w);
         const bool yin = (y0 - G::HL >= 0) && (y0 + G::TH + G::HL <= h);
-        constexpr int NQ = G::SU_W / 4;  // 21 float4 per row
-        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(su);
-        for (int i = tid; i < G::SU_H * NQ; i += 256) {
-            int r = i / NQ, q = i - r * NQ;
-            int gy = yin ? y0 - G::HL + r : mirror_idx(y0 - G::HL + r, h);
-            const float *row = uc + (long)gy * pitch;
-            int gx = x0 - 8 + 4 * q;
-            uint32_t sa = sbase + 4u * (uint32_t)(r * G::SU_W + 4 * q);
-            if (xin) {
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(row + gx) : "memory");
-            } else {
+        constexpr int NQ = G::SU_W / 4;                // 21 float4 per row
+        constexpr int RP = 256 / NQ;                   // 12 rows per pass
+        constexpr int NP = (G::SU_H + RP - 1) / RP;    // passes
+        if (tid < RP * NQ) {
+            const int q = tid % NQ, r0 = tid / NQ;
+            const int gx = x0 - 8 + 4 * q;
+            uint32_t sa = (uint32_t)__cvta_generic_to_shared(su) + 4u * (uint32_t)(r0 * G::SU_W + 4 * q);
+            if (xin && yin) {
+                const float *src = uc + (long)(y0 - G::HL + r0) * pitch + gx;
+                const long step = (long)RP * pitch;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + 4u * j),
-                                 "l"(row + mirror_idx(gx + j, w))
-                                 : "memory");
+                for (int k = 0; k < NP; ++k)
+                    if (r0 + RP * k < G::SU_H)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa + 4u * RP * G::SU_W * k),
+                                     "l"(src + step * k)
+                                     : "memory");
+            } else {
+                for (int r = r0; r < G::SU_H; r += RP, sa += 4u * RP * G::SU_W) {
+                    const float *row = uc + (long)mirror_idx(y0 - G::HL + r, h) * pitch;
+                    if (xin) {
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(row + gx) : "memory");
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa + 4u * j),
+                                         "l"(row + mirror_idx(gx + j, w))
+                                         : "memory");
+                    }
+                }
             }
         }
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
