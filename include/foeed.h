@@ -239,9 +239,14 @@ foeed_status foeed_errors(const void *u, const void *v, int w, int h, long pitch
  *   1632 x 1632 in FP64).
  *   The call allocates nothing: no cudaMalloc / cudaFree, no graph, no event;
  *   it launches the step kernels one by one on `stream`.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture. All calls on a device share the one array and
+ *   The array is part of the library's device module: the module is loaded,
+ *   and the 64 MiB taken from the device, by the first call into this library
+ *   on that device (any entry point; under CUDA's lazy module loading that can
+ *   be this one), so make a first call at set-up, outside any memory budget
+ *   that must not change. The first call of this entry point on a device also
+ *   looks up the array's device address (cudaGetSymbolAddress) with that device
+ *   current; make that first call before any stream capture. Later calls take
+ *   no device memory. All calls on a device share the one array and
  *   it keeps the previous call's contents (the solve re-initialises what it
  *   reads), so calls that overlap on the GPU (other streams, other threads)
  *   race: serialise them. report->ms is host wall time of the call.

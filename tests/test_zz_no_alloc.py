@@ -40,22 +40,45 @@ def _static_call(fd, md, ud, params, dtype_code):
     return st, rep
 
 
-@pytest.mark.parametrize("dtype,tdt,tol", [(fg.F32, torch.float32, 1e-6), (fg.F64, torch.float64, 1e-12)])
-def test_static_entry_matches_workspace_entry_twice(dtype, tdt, tol):
+@pytest.mark.parametrize("dtype,tdt", [(fg.F32, torch.float32), (fg.F64, torch.float64)])
+@pytest.mark.parametrize("n", [12, 1])
+def test_static_entry_matches_workspace_entry_twice(dtype, tdt, n):
+    """Two calls in a row (the shared array keeps the first call's contents) on two
+    image sizes, with a cycle length of 12 and of 1 (the single-step cycle copies
+    its result back into the cycle buffer): the same kernels run in the same order
+    as in foeed_inpaint, so the results are bitwise equal."""
     for call, (h, w, seed_inst) in enumerate([(96, 130, 0), (61, 47, 1)]):
         img, mask, p = synth.workload(2, h=h, w=w, instance=seed_inst)
         fd = torch.from_numpy(img).to(DEV, tdt)
         md = torch.from_numpy(mask).to(DEV)
-        ref, rrep = fg.foeed_inpaint(fd, md, 0.03, 1.0, 12, 6)
+        ref, rrep = fg.foeed_inpaint(fd, md, 0.03, 1.0, n, 6)
         ud = torch.full_like(fd, float("nan"))
-        params = fg._params(0.03, 1.0, 0.0, 12, 6)
+        params = fg._params(0.03, 1.0, 0.0, n, 6)
         st, rep = _static_call(fd, md, ud, params, dtype)
         assert st == 0, fg.lib().foeed_last_error()
         assert rep.cycles_run == rrep.cycles_run == 6
-        diff = float((ud - ref).abs().max().item())
-        assert diff <= tol, (call, diff)
+        assert torch.equal(ud, ref), (call, float((ud - ref).abs().max().item()))
         k = md.bool()
         assert torch.equal(ud[k], fd[k])
+
+
+def test_static_entry_allocates_no_device_memory():
+    """After the first call on the device (which loads the library's module and with
+    it the static array), further calls leave the device's free memory unchanged."""
+    img, mask, p = synth.workload(2, h=200, w=300)
+    fd = torch.from_numpy(img).to(DEV, torch.float32)
+    md = torch.from_numpy(mask).to(DEV)
+    ud = torch.empty_like(fd)
+    params = fg._params(0.03, 1.0, 0.0, 10, 3)
+    st, _ = _static_call(fd, md, ud, params, fg.F32)
+    assert st == 0, fg.lib().foeed_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st, _ = _static_call(fd, md, ud, params, fg.F32)
+    assert st == 0, fg.lib().foeed_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_static_entry_rejects_images_beyond_the_scratch():
