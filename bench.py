@@ -226,16 +226,28 @@ def batched_leg(fg, synth, torch, dev, stream):
     n, cycles = 25, 50
     pixels = sum(int(im.numel()) for im in imgs)
     pu = pixels * n * cycles
-    outs, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, cycles)  # warm-up
+    fg.set_tile_policy("auto")
+    fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, 1)  # warm-up: the autotuner times the tile plans here
+    plan = fg.last_tile_plan()
     ws = torch.empty(fg.workspace_bytes(1024, 1024, fg.F32), dtype=torch.uint8, device=dev)
-    times = []
-    for _ in range(2):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        outs, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, cycles, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        times.append(a.elapsed_time(b))
+
+    def timed_batch(reps=2):
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res, _ = fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, n, cycles, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(a.elapsed_time(b))
+        return res, min(times)
+
+    outs, ms = timed_batch()
+    # the same batch with 64 x 32 tiles for every image (the plan without the autotuner)
+    fg.set_tile_policy("h32")
+    outs32, ms32 = timed_batch()
+    fg.set_tile_policy("auto")
+    same_bits = all(bool(torch.equal(x, y)) for x, y in zip(outs, outs32))
     for f, m, lam in zip(imgs[:4], masks[:4], lams[:4]):  # warm the single-image path
         fg.foeed_inpaint(f, m, lam, 1.0, n, 1, workspace=ws)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -247,8 +259,12 @@ def batched_leg(fg, synth, torch, dev, stream):
     b.record(stream)
     torch.cuda.synchronize(dev)
     seq_ms = a.elapsed_time(b)
-    ms = min(times)
     return {"value": pu / (ms / 1e3), "unit": UNIT, "images": len(imgs), "pixels": pixels, "ms_per_solve": ms,
+            "tile_plan": {"images_on_64x16_tiles": plan["images_h16"], "tuned": bool(plan["tuned"]),
+                          "us_per_step_all_64x32": plan["us_h32"], "us_per_step_all_64x16": plan["us_h16"],
+                          "us_per_step_chosen": plan["us_chosen"]},
+            "fixed_64x32_value": pu / (ms32 / 1e3), "fixed_64x32_ms": ms32,
+            "autotuned_equals_fixed_bitwise": same_bits,
             "one_by_one_value": pu / (seq_ms / 1e3), "one_by_one_ms": seq_ms,
             "max_abs_diff_vs_one_by_one": diff, "fsi_cycles": cycles, "cycle_len": n}
 
@@ -410,8 +426,12 @@ def main():
     def solve():
         return fg.foeed_inpaint(fd, md, p["lam"], p["sigma"], n, cycles, workspace=ws, stream=stream)
 
+    fg.set_tile_policy("auto")
+    tile_plan = None
     for _ in range(args.warmup):
         solve()
+        if tile_plan is None:  # the first solve of this size times the tile shapes
+            tile_plan = fg.last_tile_plan()
     torch.cuda.synchronize(dev)
 
     # ---- timed region: K device-resident solves, L2 flushed between them ----
@@ -562,6 +582,7 @@ def main():
                              "L2-resident within a solve",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches_per_solve * args.steps, "roofline": roofline,
+            "tile_plan": tile_plan,
             "cpu_baseline": cpu, "clocks": clocks, **extra,
         }
         print(json.dumps(line), flush=True)

@@ -25,6 +25,7 @@ from . import build as _build
 __all__ = ["foeed_inpaint", "eed_inpaint", "foeed_inpaint_batch", "eed_inpaint_batch", "inpaint_channels",
            "foeed_inpaint_vjp", "foeed_inpaint_diff",
            "foeed_step", "eed_step", "foeed_errors", "foeed_apply_tensor_field", "workspace_bytes",
+           "set_tile_policy", "last_tile_plan",
            "Report", "FoeedError", "lib", "F32", "F64", "F32_F64U", "STATUS"]
 
 F32, F64, F32_F64U = 0, 1, 2
@@ -54,6 +55,14 @@ class _Instance(C.Structure):
 class _Report(C.Structure):
     _fields_ = [("cycles_run", C.c_int), ("last_rel_change", C.c_double), ("converged", C.c_int),
                 ("ms", C.c_float)]
+
+
+class _TilePlan(C.Structure):
+    _fields_ = [("tile_h", C.c_int), ("images", C.c_int), ("images_h16", C.c_int), ("tuned", C.c_int),
+                ("us_h32", C.c_float), ("us_h16", C.c_float), ("us_chosen", C.c_float)]
+
+
+TILE_POLICY = {"auto": 0, "h16": 16, "h32": 32, 0: 0, 16: 16, 32: 32}
 
 
 @dataclass
@@ -103,6 +112,10 @@ def lib():
         L.foeed_errors_workspace_bytes.restype = sz
         L.foeed_errors.argtypes = [vp, vp, i, i, C.c_long, i, vp, sz, vp, C.POINTER(C.c_double)]
         L.foeed_errors.restype = i
+        L.foeed_set_tile_policy.argtypes = [i]
+        L.foeed_set_tile_policy.restype = i
+        L.foeed_last_tile_plan.argtypes = [C.POINTER(_TilePlan)]
+        L.foeed_last_tile_plan.restype = i
         L.foeed_last_error.restype = C.c_char_p
         L.foeed_version.restype = C.c_char_p
         _lib = L
@@ -157,6 +170,20 @@ def _as_device_image(a, dtype, device):
     if t.stride(1) != 1:
         t = t.contiguous()
     return t
+
+
+def set_tile_policy(policy="auto"):
+    """Tile shape of the register-blocked FP32 kernels for later calls on this host
+    thread: "auto" (timed once per size and kept), "h32" or "h16" (64 x 32 or 64 x 16
+    tiles for every image). Results are bitwise the same under every policy."""
+    _check(lib().foeed_set_tile_policy(TILE_POLICY[policy]))
+
+
+def last_tile_plan():
+    """The tile plan of the last solve on this thread (dict of foeed_tile_plan)."""
+    t = _TilePlan()
+    _check(lib().foeed_last_tile_plan(C.byref(t)))
+    return {k: getattr(t, k) for k, _ in _TilePlan._fields_}
 
 
 def workspace_bytes(w, h, dtype=F32):

@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <climits>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -234,7 +236,8 @@ struct StepCall {
     Ctl *ctl;
     double *partials;
     int residual, check_done;
-    int pdl;  // launch with a programmatic dependency on the previous kernel
+    int pdl;     // launch with a programmatic dependency on the previous kernel
+    int tile_h;  // register-blocked FP32 kernel: tile height 16 or 32 (0: size rule)
 };
 
 template <typename T>
@@ -265,6 +268,7 @@ StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
     a.residual = c.residual;
     a.check_done = c.check_done;
     a.pdl = c.pdl;
+    a.tile_h = c.tile_h;
     return a;
 }
 
@@ -304,10 +308,119 @@ cudaError_t launch_step(bool eed, foeed_dtype d, const StepCall *c, const foeed_
 }
 
 // ---------------------------------------------------------------------------
+// Tile-shape autotuner of the register-blocked FP32 kernels (64 x 32 or 64 x 16
+// output tiles; both give the same bits, only the time differs).
+
+thread_local int g_tile_policy = FOEED_TILES_AUTO;
+thread_local foeed_tile_plan g_last_plan = {};
+
+struct TuneKey {
+    int dev, eed, R, f64u, w, h, count, pad;
+    unsigned long long sizes;  // FNV-1a hash of a batch's image sizes (0 for one image)
+    bool operator<(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) < 0; }
+};
+
+struct TuneVal {
+    int choice;  // single image: tile height; batch: tile-count threshold of the 64 x 16 images
+    float us_h32, us_h16, us_chosen;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+bool tune_lookup(const TuneKey &k, TuneVal *v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+void tune_store(const TuneKey &k, const TuneVal &v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[k] = v;
+}
+
+// Mean microseconds of `reps` back-to-back calls of launch() on s after one
+// untimed call; < 0 if a launch or an event fails.
+template <typename F>
+float time_launches(F launch, cudaStream_t s, int reps)
+{
+    EventPair ev;
+    if (ev.create() != cudaSuccess) return -1.f;
+    if (launch() != cudaSuccess) return -1.f;
+    if (cudaEventRecord(ev.e[0], s) != cudaSuccess) return -1.f;
+    for (int i = 0; i < reps; ++i)
+        if (launch() != cudaSuccess) return -1.f;
+    if (cudaEventRecord(ev.e[1], s) != cudaSuccess || cudaEventSynchronize(ev.e[1]) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]) != cudaSuccess) return -1.f;
+    return 1000.f * ms / reps;
+}
+
+constexpr int kTuneReps = 3;
+
+// Tile height of a single-image solve whose initial image is already in buffer C
+// of the workspace: the thread's fixed policy, the cached choice for this
+// (device, size, method, radius, precision), or the faster of 64 x 32 and 64 x 16
+// tiles, timed on one step C -> A (buffer A is overwritten by the solve's first
+// step). 0 when the generic kernel runs.
+foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L, char *ws,
+                           cudaStream_t s, int *tile_h)
+{
+    g_last_plan = foeed_tile_plan{};
+    g_last_plan.images = 1;
+    *tile_h = 0;
+    if (d == FOEED_F64 || !fast_params(eed, p)) return FOEED_OK;
+    if (g_tile_policy != FOEED_TILES_AUTO) {
+        *tile_h = g_tile_policy;
+    } else {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        TuneKey k;
+        std::memset(&k, 0, sizeof(k));
+        k.dev = dev; k.eed = eed; k.R = gauss_radius(p.sigma); k.f64u = d == FOEED_F32_F64U; k.w = w; k.h = h;
+        k.count = 1;
+        TuneVal v;
+        if (tune_lookup(k, &v)) {
+            *tile_h = v.choice;
+        } else {
+            StepCall c{};
+            c.uprev = ws + L.bufC; c.ucur = ws + L.bufC; c.unext = ws + L.bufA;
+            c.mask = reinterpret_cast<const uint8_t *>(ws + L.mask);
+            c.w = w; c.h = h; c.pitch = L.P; c.alpha = 1.0; c.tau = default_tau(eed, p.tau);
+            CK(launch_step(eed, d, nullptr, p, s));
+            float us[2];
+            const int th[2] = {32, 16};
+            for (int i = 0; i < 2; ++i) {
+                c.tile_h = th[i];
+                us[i] = time_launches([&] { return launch_step(eed, d, &c, p, s); }, s, kTuneReps);
+                if (us[i] < 0.f) return fail(FOEED_ERR_CUDA, "timing the tile shapes: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+            v.choice = us[1] < us[0] ? 16 : 32;
+            v.us_h32 = us[0];
+            v.us_h16 = us[1];
+            v.us_chosen = us[1] < us[0] ? us[1] : us[0];
+            tune_store(k, v);
+            g_last_plan.tuned = 1;
+            g_last_plan.us_h32 = v.us_h32;
+            g_last_plan.us_h16 = v.us_h16;
+            g_last_plan.us_chosen = v.us_chosen;
+            *tile_h = v.choice;
+        }
+    }
+    g_last_plan.tile_h = *tile_h;
+    g_last_plan.images_h16 = *tile_h == 16;
+    return FOEED_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Cycle graphs: one captured FSI cycle per (method, sizes, params, buffers).
 
 struct GraphKey {
-    int eed, dtype, w, h, n, g, mu3, dev;
+    int eed, dtype, w, h, n, g, mu3, dev, tile_h, pad;
     double lambda, sigma, tau;
     const void *base;
     long pitch;
@@ -330,7 +443,7 @@ thread_local unsigned long long g_clock = 0;
 thread_local cudaStream_t g_capture_stream[64] = {};
 
 foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L,
-                           char *ws, int dev, cudaGraphExec_t *out)
+                           char *ws, int dev, int tile_h, cudaGraphExec_t *out)
 {
     cudaStream_t cs = g_capture_stream[dev & 63];
     if (!cs) {
@@ -355,6 +468,7 @@ foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w
         c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
         c.tau = tau;
         c.ctl = ctl; c.partials = partials; c.check_done = 1;
+        c.tile_h = tile_h;
         const bool last = (k == n - 1);
         if (k == 0) { c.uprev = C; c.ucur = C; c.unext = A; }
         else if (k == 1) { c.uprev = C; c.ucur = A; c.unext = last ? C : B; }
@@ -378,7 +492,7 @@ foeed_status capture_cycle(bool eed, foeed_dtype d, const foeed_params &p, int w
 }
 
 foeed_status get_cycle_graph(bool eed, foeed_dtype d, const foeed_params &p, int w, int h, const Layout &L,
-                             char *ws, cudaGraphExec_t *out)
+                             char *ws, int tile_h, cudaGraphExec_t *out)
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -387,7 +501,7 @@ foeed_status get_cycle_graph(bool eed, foeed_dtype d, const foeed_params &p, int
     key.eed = eed; key.dtype = d; key.w = w; key.h = h; key.n = p.cycle_len;
     key.g = p.diffusivity; key.mu3 = eed ? 0 : p.mu3_mode; key.dev = dev;
     key.lambda = p.lambda; key.sigma = p.sigma; key.tau = default_tau(eed, p.tau);
-    key.base = ws; key.pitch = L.P;
+    key.base = ws; key.pitch = L.P; key.tile_h = tile_h;
     int victim = 0;
     for (int i = 0; i < kCache; ++i) {
         if (g_cache[i].exec && g_cache[i].key == key) {
@@ -398,7 +512,7 @@ foeed_status get_cycle_graph(bool eed, foeed_dtype d, const foeed_params &p, int
         if (g_cache[i].stamp < g_cache[victim].stamp) victim = i;
     }
     cudaGraphExec_t exec = nullptr;
-    foeed_status st = capture_cycle(eed, d, p, w, h, L, ws, dev, &exec);
+    foeed_status st = capture_cycle(eed, d, p, w, h, L, ws, dev, tile_h, &exec);
     if (st != FOEED_OK) return st;
     if (g_cache[victim].exec) cudaGraphExecDestroy(g_cache[victim].exec);
     g_cache[victim].key = key;
@@ -446,9 +560,6 @@ foeed_status inpaint(bool eed, const void *f, const uint8_t *mask, void *u_inout
     char *ws = static_cast<char *>(workspace);
     Ctl *dctl = reinterpret_cast<Ctl *>(ws + L.ctl);
 
-    cudaGraphExec_t exec = nullptr;
-    if ((st = get_cycle_graph(eed, d, p, w, h, L, ws, &exec))) return st;
-
     Ctl h0;
     std::memset(&h0, 0, sizeof(h0));
     h0.tol = p.tol;
@@ -459,6 +570,10 @@ foeed_status inpaint(bool eed, const void *f, const uint8_t *mask, void *u_inout
     CK(cudaEventRecord(ev0, s));
     CK(d == FOEED_F64 ? launch_prep<double>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s)
                       : launch_prep<float>(f, mask, u_inout, w, h, pitch, L, ws, p.init_mode, s));
+    int tile_h = 0;
+    if ((st = choose_tile_h(eed, d, p, w, h, L, ws, s, &tile_h))) return st;
+    cudaGraphExec_t exec = nullptr;
+    if ((st = get_cycle_graph(eed, d, p, w, h, L, ws, tile_h, &exec))) return st;
     const int every = p.check_every > 0 ? p.check_every : 8;
     Ctl hc;
     std::memset(&hc, 0, sizeof(hc));
@@ -505,6 +620,7 @@ foeed_status step(bool eed, const void *u_prev, const void *u_cur, void *u_next,
     c.w = w; c.h = h; c.pitch = pitch; c.alpha = alpha;
     c.tau = default_tau(eed, params->tau);
     c.c0 = nullptr; c.ctl = nullptr; c.partials = nullptr; c.residual = 0; c.check_done = 0;
+    c.tile_h = g_tile_policy;
     CK(launch_step(eed, d, nullptr, *params, static_cast<cudaStream_t>(stream)));
     CK(launch_step(eed, d, &c, *params, static_cast<cudaStream_t>(stream)));
     return FOEED_OK;
@@ -593,6 +709,21 @@ foeed_status foeed_apply_tensor_field(const void *u, const void *d, void *Pu, in
     if (!u || !d || !Pu) return fail(FOEED_ERR_ARG, "NULL pointer");
     if (Pu == u) return fail(FOEED_ERR_ARG, "Pu must not alias u");
     CK(apply_field(u, d, Pu, w, h, pitch, dtype == FOEED_F64, static_cast<cudaStream_t>(stream)));
+    return FOEED_OK;
+}
+
+foeed_status foeed_set_tile_policy(int policy)
+{
+    if (policy != FOEED_TILES_AUTO && policy != FOEED_TILES_H16 && policy != FOEED_TILES_H32)
+        return fail(FOEED_ERR_ARG, "unknown tile policy %d", policy);
+    g_tile_policy = policy;
+    return FOEED_OK;
+}
+
+foeed_status foeed_last_tile_plan(foeed_tile_plan *out)
+{
+    if (!out) return fail(FOEED_ERR_ARG, "NULL pointer");
+    *out = g_last_plan;
     return FOEED_OK;
 }
 
@@ -726,6 +857,7 @@ foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, voi
         c.w = w; c.h = h; c.pitch = P;
         c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
         c.tau = tau;
+        c.tile_h = g_tile_policy;
         return launch_step(false, d, &c, p, s);
     };
 
@@ -829,8 +961,41 @@ struct BatchPlan {
     std::vector<Layout> lay;
     std::vector<size_t> off;  // workspace offset of each image's region
     size_t inst_off, tiles_off, total;
-    int ntiles;
+    int ntiles;               // capacity of the tile list (every image on 64 x 16 tiles)
 };
+
+// Device tables of one tile plan of a batch: images with fewer than `thresh`
+// 64 x 32 tiles run on 64 x 16 tiles, the others on 64 x 32 tiles (thresh 0:
+// every image on 64 x 32; INT_MAX: every image on 64 x 16). hi / ht receive the
+// image table and the (image, tile) work list.
+void batch_tables(const foeed_instance *inst, int count, const BatchPlan &bp, char *ws, int thresh,
+                  std::vector<BatchInst> &hi, std::vector<int2> &ht, int *images_h16)
+{
+    hi.resize(count);
+    ht.clear();
+    *images_h16 = 0;
+    for (int i = 0; i < count; ++i) {
+        const Layout &L = bp.lay[i];
+        char *b = ws + bp.off[i];
+        BatchInst &I = hi[i];
+        I.C = reinterpret_cast<float *>(b + L.bufC);
+        I.A = reinterpret_cast<float *>(b + L.bufA);
+        I.B = reinterpret_cast<float *>(b + L.bufB);
+        I.mask = reinterpret_cast<const uint8_t *>(b + L.mask);
+        I.w = inst[i].w;
+        I.h = inst[i].h;
+        I.pitch = L.P;
+        I.c4 = float(0.25 / (inst[i].lambda * inst[i].lambda));
+        const long long n32 = (long long)((inst[i].w + 63) / 64) * ((inst[i].h + 31) / 32);
+        I.th = n32 < thresh ? 16 : 32;
+        *images_h16 += I.th == 16;
+        I.ntx = (inst[i].w + 63) / 64;
+        I.nty = (inst[i].h + I.th - 1) / I.th;
+        I.ctl = reinterpret_cast<Ctl *>(b + L.ctl);
+        I.partials = reinterpret_cast<double *>(b + L.partials);
+        for (int k = 0; k < I.ntx * I.nty; ++k) ht.push_back(make_int2(i, k));
+    }
+}
 
 foeed_status batch_plan(const foeed_instance *inst, int count, foeed_dtype d, BatchPlan *bp)
 {
@@ -848,7 +1013,7 @@ foeed_status batch_plan(const foeed_instance *inst, int count, foeed_dtype d, Ba
             std::snprintf(msg, sizeof(msg), "%s", g_err);
             return fail(st, "image %d: %s", i, msg);
         }
-        ntiles += (long long)((inst[i].w + 63) / 64) * ((inst[i].h + 31) / 32);
+        ntiles += (long long)((inst[i].w + 63) / 64) * ((inst[i].h + 15) / 16);  // the most tiles any plan has
     }
     if (ntiles > (1LL << 30)) return fail(FOEED_ERR_ARG, "too many tiles");
     bp->ntiles = (int)ntiles;
@@ -902,31 +1067,6 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     const int R = gauss_radius(p.sigma);
     const double tau = default_tau(eed, p.tau);
 
-    // device tables: one entry per image, one (image, tile) pair per CTA
-    std::vector<BatchInst> hi(count);
-    std::vector<int2> ht((size_t)bp.ntiles);
-    size_t t = 0;
-    for (int i = 0; i < count; ++i) {
-        const Layout &L = bp.lay[i];
-        char *b = ws + bp.off[i];
-        BatchInst &I = hi[i];
-        I.C = reinterpret_cast<float *>(b + L.bufC);
-        I.A = reinterpret_cast<float *>(b + L.bufA);
-        I.B = reinterpret_cast<float *>(b + L.bufB);
-        I.mask = reinterpret_cast<const uint8_t *>(b + L.mask);
-        I.w = inst[i].w;
-        I.h = inst[i].h;
-        I.pitch = L.P;
-        I.c4 = float(0.25 / (inst[i].lambda * inst[i].lambda));
-        I.ntx = (inst[i].w + 63) / 64;
-        I.nty = (inst[i].h + 31) / 32;
-        I.ctl = reinterpret_cast<Ctl *>(b + L.ctl);
-        I.partials = reinterpret_cast<double *>(b + L.partials);
-        for (int k = 0; k < I.ntx * I.nty; ++k) ht[t++] = make_int2(i, k);
-    }
-    CK(cudaMemcpyAsync(ws + bp.inst_off, hi.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + bp.tiles_off, ht.data(), sizeof(int2) * ht.size(), cudaMemcpyHostToDevice, s));
-
     // per-image set-up: control block, internal mask, initial image
     Ctl h0;
     std::memset(&h0, 0, sizeof(h0));
@@ -936,17 +1076,93 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1];
     CK(cudaEventRecord(ev0, s));
     for (int i = 0; i < count; ++i) {
-        CK(cudaMemcpyAsync(hi[i].ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        const Layout &L = bp.lay[i];
+        CK(cudaMemcpyAsync(ws + bp.off[i] + L.ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
         CK(launch_prep<float>(inst[i].f, inst[i].mask, inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch,
                               bp.lay[i], ws + bp.off[i], p.init_mode, s));
     }
 
-    // one FSI cycle = n launches over the work list, captured once
+    // tile plan: the thread's fixed policy, the cached choice for this list of
+    // sizes, or the fastest candidate plan timed on one step C -> A over all
+    // images (buffer A is overwritten by the solve's first step)
     StepCall c{};
     c.w = 1; c.h = 1; c.pitch = 4;
     c.tau = tau;
     StepArgs<float> a = make_args<float>(c, p);
     CK(batch_step(nullptr, nullptr, 0, R, f64u, s));
+    std::vector<BatchInst> hi;
+    std::vector<int2> ht;
+    int images_h16 = 0;
+    BatchArgs bt;
+    bt.inst = reinterpret_cast<const BatchInst *>(ws + bp.inst_off);
+    bt.tiles = reinterpret_cast<const int2 *>(ws + bp.tiles_off);
+    bt.role = kRoleFirst;
+    bt.last = 0;
+    auto upload = [&](int thresh) -> cudaError_t {
+        batch_tables(inst, count, bp, ws, thresh, hi, ht, &images_h16);
+        cudaError_t e = cudaMemcpyAsync(ws + bp.inst_off, hi.data(), sizeof(BatchInst) * count,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + bp.tiles_off, ht.data(), sizeof(int2) * ht.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables are rebuilt for the next plan
+        return e;
+    };
+    g_last_plan = foeed_tile_plan{};
+    g_last_plan.images = count;
+    int thresh = g_tile_policy == FOEED_TILES_H16 ? INT_MAX : 0;
+    if (g_tile_policy == FOEED_TILES_AUTO) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        TuneKey k;
+        std::memset(&k, 0, sizeof(k));
+        k.dev = dev; k.eed = eed; k.R = R; k.f64u = f64u; k.count = count;
+        unsigned long long hsh = 1469598103934665603ULL;
+        std::vector<long long> n32(count);
+        for (int i = 0; i < count; ++i) {
+            hsh = (hsh ^ (unsigned)inst[i].w) * 1099511628211ULL;
+            hsh = (hsh ^ (unsigned)inst[i].h) * 1099511628211ULL;
+            n32[i] = (long long)((inst[i].w + 63) / 64) * ((inst[i].h + 31) / 32);
+        }
+        k.sizes = hsh;
+        TuneVal v;
+        if (tune_lookup(k, &v)) {
+            thresh = v.choice;
+        } else {
+            // candidates: every image on 64 x 32, every image on 64 x 16, and the images
+            // below each quartile of the batch's 64 x 32 tile counts on 64 x 16
+            std::vector<long long> sorted = n32;
+            std::sort(sorted.begin(), sorted.end());
+            std::vector<int> cand = {0, INT_MAX};
+            for (int qn = 1; qn <= 3; ++qn) {
+                const long long t = sorted[(size_t)(count - 1) * qn / 4] + 1;
+                if (t < INT_MAX && std::find(cand.begin(), cand.end(), (int)t) == cand.end()) cand.push_back((int)t);
+            }
+            float best = -1.f;
+            v.us_h32 = v.us_h16 = 0.f;
+            for (size_t ci = 0; ci < cand.size(); ++ci) {
+                CK(upload(cand[ci]));
+                const int nt = (int)ht.size();
+                const float us = time_launches([&] { return batch_step(&a, &bt, nt, R, f64u, s); }, s, kTuneReps);
+                if (us < 0.f)
+                    return fail(FOEED_ERR_CUDA, "timing the tile plans: %s", cudaGetErrorString(cudaGetLastError()));
+                if (cand[ci] == 0) v.us_h32 = us;
+                if (cand[ci] == INT_MAX) v.us_h16 = us;
+                if (best < 0.f || us < best) { best = us; v.choice = cand[ci]; }
+            }
+            v.us_chosen = best;
+            tune_store(k, v);
+            g_last_plan.tuned = 1;
+            g_last_plan.us_h32 = v.us_h32;
+            g_last_plan.us_h16 = v.us_h16;
+            g_last_plan.us_chosen = v.us_chosen;
+            thresh = v.choice;
+        }
+    }
+    CK(upload(thresh));
+    g_last_plan.images_h16 = images_h16;
+    const int ntiles = (int)ht.size();
+
+    // one FSI cycle = n launches over the work list, captured once
     int dev = 0;
     CK(cudaGetDevice(&dev));
     cudaStream_t cs = g_capture_stream[dev & 63];
@@ -967,7 +1183,7 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
         a.alpha_t = float(a.alpha);
         a.residual = b.last;
         a.pdl = k > 0;
-        err = batch_step(&a, &b, bp.ntiles, R, f64u, cs);
+        err = batch_step(&a, &b, ntiles, R, f64u, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1123,6 +1339,7 @@ extern "C" foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask,
             c.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
             c.tau = tau;
             c.ctl = dctl; c.partials = partials; c.check_done = 1;
+            c.tile_h = g_tile_policy;
             const bool last = (k == n - 1);
             if (k == 0) { c.uprev = C; c.ucur = C; c.unext = A; }
             else if (k == 1) { c.uprev = C; c.ucur = A; c.unext = last ? C : B; }

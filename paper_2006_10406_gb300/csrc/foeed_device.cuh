@@ -61,6 +61,7 @@ struct StepArgs {
     int residual;        // 1: accumulate the cycle residual and finalise it
     int check_done;      // 1: return at once when ctl->done is set
     int pdl;             // host only: launch with programmatic dependency on the previous kernel
+    int tile_h;          // host only: register-blocked FP32 kernel's tile height (16, 32; 0: size rule)
 };
 
 // Launches kern over grid with the arguments a, as an ordinary launch or, when
@@ -93,7 +94,8 @@ struct BatchInst {
     int w, h;
     long pitch;
     float c4;             // 1/(4 lambda^2) of this image
-    int ntx, nty;         // its 64 x 32 tile grid
+    int th;               // its tile height (32 or 16)
+    int ntx, nty;         // its 64 x th tile grid
     Ctl *ctl;             // its control block (cycle residual, stop flag)
     double *partials;     // its per-tile residual partials
 };

@@ -505,8 +505,10 @@ __device__ __forceinline__ void finish_cycle_residual(double rnum, double rden, 
     }
 }
 
-// Images with fewer 64 x 32 tiles than this run on 64 x 16 tiles: they fill
-// less than a wave of the GPU, and a step's time is the latency of one tile.
+// The size rule used when no tile height is given (the launches that are not
+// autotuned): images with fewer 64 x 32 tiles than this run on 64 x 16 tiles,
+// as they fill less than a wave of the GPU and a step's time is then the
+// latency of one tile.
 constexpr long long kFastSmallTiles = 304;
 
 // One FSI step over one image, one CTA per 64 x TH tile.
@@ -558,7 +560,10 @@ __global__ void __launch_bounds__(256) fsi_batch_step_fast(const StepArgs<float>
     im.c4 = I.c4;
     const int ty = tl.y / I.ntx, tx = tl.y - ty * I.ntx;
     double rnum = 0.0, rden = 0.0;
-    fast_tile<R, EED, U>(p, im, tx * FastTile<R, EED>::TW, ty * FastTile<R, EED>::TH, sm, rnum, rden);
+    if (I.th == 16)
+        fast_tile<R, EED, U, 16>(p, im, tx * 64, ty * 16, sm, rnum, rden);
+    else
+        fast_tile<R, EED, U, 32>(p, im, tx * 64, ty * 32, sm, rnum, rden);
     if (b.last) finish_cycle_residual(rnum, rden, I.ctl, I.partials, I.ntx * I.nty, tl.y, red);
 }
 
@@ -598,7 +603,8 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
         return cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G16::SMEM);
     }
     const int ntx = (ap->w + 63) / 64;
-    if ((long long)ntx * ((ap->h + 31) / 32) < kFastSmallTiles) {
+    const bool h16 = ap->tile_h == 16 || (ap->tile_h != 32 && (long long)ntx * ((ap->h + 31) / 32) < kFastSmallTiles);
+    if (h16) {
         dim3 grid(ntx, (ap->h + 15) / 16);
         return launch_step_kernel(k16, grid, 256, G16::SMEM, s, *ap);
     }

@@ -153,3 +153,25 @@ def test_messages_are_per_call():
     first = last_error()
     assert inpaint(p=params(lam=-1.0)) == ERR_ARG
     assert last_error() != first and "lambda" in last_error()
+
+
+def test_tile_policy_arguments_are_checked_on_the_host():
+    """foeed_set_tile_policy accepts AUTO (0), 16 and 32 only; foeed_last_tile_plan
+    rejects NULL. Neither touches the GPU."""
+    import ctypes as C
+
+    import paper_2006_10406_gb300 as fg
+    L = fg.lib()
+    try:
+        for bad in (1, 8, 64, -1):
+            assert L.foeed_set_tile_policy(bad) == 1
+            assert b"tile policy" in L.foeed_last_error()
+        for good in (16, 32, 0):
+            assert L.foeed_set_tile_policy(good) == 0
+        assert L.foeed_last_tile_plan(None) == 1
+        plan = fg._TilePlan()
+        assert L.foeed_last_tile_plan(C.byref(plan)) == 0
+        with pytest.raises(KeyError):
+            fg.set_tile_policy("h8")
+    finally:
+        L.foeed_set_tile_policy(0)

@@ -448,6 +448,62 @@ def _batch_case(seed=0, sizes=((64, 64), (96, 130), (33, 200), (128, 64), (7, 9)
     return imgs, masks, lams
 
 
+# --------------------------------------------------------------------------
+# the tile-shape autotuner: every policy gives bitwise the same results
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("shape", [(512, 512), (630, 1030), (96, 2100)])
+def test_autotuned_solve_equals_each_fixed_tile_shape(method, shape):
+    img, mask, p = synth.workload(2, h=shape[0], w=shape[1], instance=7)
+    f, m = _dev(img, torch.float32), _dev(mask, torch.uint8)
+    solve = fg.foeed_inpaint if method == 0 else fg.eed_inpaint
+    lam, sigma = 0.03, 1.0
+    try:
+        fg.set_tile_policy("auto")
+        ua, _ = solve(f, m, lam, sigma, 8, 3)
+        plan = fg.last_tile_plan()
+        assert plan["images"] == 1 and plan["tile_h"] in (16, 32)
+        if plan["tuned"]:
+            assert plan["us_h32"] > 0 and plan["us_h16"] > 0
+            assert plan["us_chosen"] == min(plan["us_h32"], plan["us_h16"])
+            assert plan["tile_h"] == (16 if plan["us_h16"] < plan["us_h32"] else 32)
+        ua2, _ = solve(f, m, lam, sigma, 8, 3)
+        again = fg.last_tile_plan()
+        assert again["tuned"] == 0 and again["tile_h"] == plan["tile_h"]  # the choice is cached
+        assert torch.equal(ua, ua2)
+        for pol, th in (("h32", 32), ("h16", 16)):
+            fg.set_tile_policy(pol)
+            u, _ = solve(f, m, lam, sigma, 8, 3)
+            assert fg.last_tile_plan()["tile_h"] == th
+            assert torch.equal(u, ua), pol
+    finally:
+        fg.set_tile_policy("auto")
+
+
+@pytest.mark.parametrize("method", ["foeed", "eed"])
+def test_autotuned_batch_equals_each_fixed_tile_plan(method):
+    cases = synth.batched_workload(14, sides=(128, 256, 384, 640))
+    imgs = [_dev(c[0], torch.float32) for c in cases]
+    masks = [_dev(c[1], torch.uint8) for c in cases]
+    lams = [float(c[2]) for c in cases]
+    solve = fg.foeed_inpaint_batch if method == "foeed" else fg.eed_inpaint_batch
+    try:
+        fg.set_tile_policy("auto")
+        ua, _ = solve(imgs, masks, lams, 1.0, 6, 3)
+        plan = fg.last_tile_plan()
+        assert plan["images"] == len(imgs) and 0 <= plan["images_h16"] <= len(imgs)
+        if plan["tuned"]:
+            assert 0 < plan["us_chosen"] <= min(plan["us_h32"], plan["us_h16"])
+        for pol, nh16 in (("h32", 0), ("h16", len(imgs))):
+            fg.set_tile_policy(pol)
+            u, _ = solve(imgs, masks, lams, 1.0, 6, 3)
+            assert fg.last_tile_plan()["images_h16"] == nh16
+            for a, b in zip(u, ua):
+                assert torch.equal(a, b), pol
+    finally:
+        fg.set_tile_policy("auto")
+
+
 @pytest.mark.parametrize("n", [2, 3, 25])
 @pytest.mark.parametrize("dtype", ["f32", "f32_f64u"])
 def test_batch_equals_single_image_solves(n, dtype):
