@@ -541,8 +541,9 @@ def main():
             # the other arithmetic modes of the same solve (the FP64 GPU solve is the parity-tested reference)
             extra["precisions"] = {
                 "f64": {"value": pu_per_solve / (ms64 / 1e3), "unit": UNIT, "ms_per_solve": ms64},
-                "f32_storage_f64_update": {
+                "f32_storage_two_float_update": {
                     "value": pu_per_solve / (msmx / 1e3), "unit": UNIT, "ms_per_solve": msmx,
+                    "update": "FSI update in two-float arithmetic (pairs of floats), rounded to float once",
                     "max_abs_vs_f64_gpu": float((umx.double() - u64).abs().max().item()),
                     "psnr_db": mmx[2], "psnr_delta_vs_f64_db": abs(mmx[2] - m64[2])}}
             del ws64, fd64

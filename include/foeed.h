@@ -30,8 +30,11 @@
  *     stream); calls that share a workspace must not overlap on the GPU.
  *   - dtype selects the storage and arithmetic type of the images: FOEED_F32
  *     (stencils in float, all reductions in double) or FOEED_F64 (double throughout).
- *     The mixed-precision FOEED_F32_F64U keeps images in float but evaluates the
- *     FSI extrapolation update in double.
+ *     The mixed-precision FOEED_F32_F64U keeps images and stencils in float but
+ *     evaluates the FSI extrapolation update u^{k-1} + alpha ((u^k - tau P u^k) -
+ *     u^{k-1}) in extended precision and rounds it to float once: in two-float
+ *     arithmetic (pairs of floats, error-free sums and FMA products) in the
+ *     register-blocked kernel, in double in the generic one.
  */
 #ifndef FOEED_H
 #define FOEED_H

@@ -257,6 +257,8 @@ StepArgs<T> make_args(const StepCall &c, const foeed_params &p)
     a.lambda = p.lambda;
     a.alpha_t = T(c.alpha);
     a.tau_t = T(c.tau);
+    a.alpha_lo = T(c.alpha - double(a.alpha_t));
+    a.tau_lo = T(c.tau - double(a.tau_t));
     a.l2 = T(p.lambda * p.lambda);
     a.inv_l2 = T(1.0 / (p.lambda * p.lambda));
     a.c4 = T(0.25 / (p.lambda * p.lambda));
@@ -1181,6 +1183,7 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
         b.last = k == n - 1;
         a.alpha = (4.0 * k + 2.0) / (2.0 * k + 3.0);
         a.alpha_t = float(a.alpha);
+        a.alpha_lo = float(a.alpha - double(a.alpha_t));
         a.residual = b.last;
         a.pdl = k > 0;
         err = batch_step(&a, &b, ntiles, R, f64u, cs);

@@ -52,6 +52,7 @@ struct StepArgs {
     double lambda;
     // the same constants pre-rounded to T on the host (no per-thread FP64 work)
     T alpha_t, tau_t;
+    T alpha_lo, tau_lo;  // alpha - alpha_t, tau - tau_t: alpha and tau as two-word values (hi + lo)
     T l2, inv_l2;  // lambda^2, 1/lambda^2
     T c4;          // 1/(4 lambda^2): lambda1/lambda^2 = |2 grad u_sigma|^2 * c4
     int g_kind, mu3_mode;

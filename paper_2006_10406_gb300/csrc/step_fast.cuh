@@ -46,6 +46,46 @@ __device__ __forceinline__ float sqrt_fast(float x)
     return r;
 }
 
+// Error-free transformations in FP32 arithmetic: a + b = s + e exactly with
+// s = fl(a + b) (Knuth's TwoSum, six operations, no ordering of a and b needed),
+// and a * b = p + e exactly with p = fl(a * b) (the FMA form of TwoProduct in
+// Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26(6), 2005).
+__device__ __forceinline__ void two_sum(const float a, const float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(const float a, const float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// The masked FSI update u^{k-1} + alpha ((u^k - tau P u^k) - u^{k-1}) (Sec. 3.3)
+// of float operands, with alpha and tau given as two-word values (hi + lo),
+// carried in two-float arithmetic and rounded to float once: every
+// intermediate is held to about 2^-44 of the operands' size, so the result is
+// the float nearest the exact update, as an evaluation in double gives, except
+// where that value lies that close to a rounding boundary.
+__device__ __forceinline__ float fsi_update_ff(const float up, const float u, const float P, const float a_hi,
+                                               const float a_lo, const float t_hi, const float t_lo)
+{
+    float th, tl, eh, el, dh, dl, qh, ql, sh, sl;
+    two_prod(t_hi, P, th, tl);
+    tl = __fmaf_rn(t_lo, P, tl);   // tau P = th + tl
+    two_sum(u, -th, eh, el);
+    el = __fsub_rn(el, tl);        // u - tau P = eh + el
+    two_sum(eh, -up, dh, dl);
+    dl = __fadd_rn(dl, el);        // (u - tau P) - u^{k-1} = dh + dl
+    two_prod(a_hi, dh, qh, ql);
+    ql = __fmaf_rn(a_hi, dl, ql);
+    ql = __fmaf_rn(a_lo, dh, ql);  // alpha ((u - tau P) - u^{k-1}) = qh + ql
+    two_sum(up, qh, sh, sl);
+    return __fadd_rn(sh, __fadd_rn(sl, ql));
+}
+
 // Eight consecutive floats from shared memory (two float4 loads; s is 16-byte aligned).
 __device__ __forceinline__ void ld8(const float *s, float *o)
 {
@@ -170,8 +210,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     float *sx = su + G::SU_W * G::SU_H;
     float *st = sx;  // aliases sx: written in stage D, after the last read of sx in stage C
     float *ss = sx + G::SXT;
-    const U alpha = sizeof(U) == sizeof(float) ? U(p.alpha_t) : U(p.alpha);
-    const U tau = sizeof(U) == sizeof(float) ? U(p.tau_t) : U(p.tau);
+    const float alpha = p.alpha_t, tau = p.tau_t;
 
     const int tid = threadIdx.x;
     const int w = im.w, h = im.h;
@@ -462,10 +501,12 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
             for (int k = 0; k < 4; ++k) {
                 if ((pre_mk[e] >> (8 * k)) & 0xffu) {
                     un[k] = ucv[k];
+                } else if (sizeof(U) == sizeof(double)) {  // the extended-precision update
+                    un[k] = fsi_update_ff(upv[k], ucv[k], Pu[k], p.alpha_t, p.alpha_lo, p.tau_t, p.tau_lo);
                 } else {
-                    U up = U(upv[k]);
-                    const U ex = fma(-tau, U(Pu[k]), U(ucv[k]));  // u^k - tau P u^k
-                    un[k] = float(fma(alpha, ex - up, up));
+                    const float up = upv[k];
+                    const float ex = __fmaf_rn(-tau, Pu[k], ucv[k]);  // u^k - tau P u^k
+                    un[k] = __fmaf_rn(alpha, __fsub_rn(ex, up), up);
                 }
             }
             if (p.residual) {

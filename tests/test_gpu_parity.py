@@ -136,7 +136,9 @@ def test_inpaint_workload1_f64(method):
 @pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("dtype", ["f32", "f32_f64u"])
 def test_inpaint_workload1_f32(method, dtype):
-    """Same solve in FP32 storage: max-abs <= 2e-4, PSNR within 0.01 dB of the oracle's."""
+    """Same solve in FP32 storage: max-abs <= 2e-4, PSNR within 0.01 dB of the oracle's.
+    With the two-float FSI update (f32_f64u) the error is that of the FP32 stencils
+    alone: max-abs <= 2e-6 against the oracle run on the same FP32-rounded input."""
     img, mask, p = synth.workload(1)
     ref, st, info = O.inpaint(method, img, mask, p["sigma"], p["lam"], p["cycle_len"], p["max_cycles"])
     f32 = img.astype(np.float32)
@@ -145,6 +147,10 @@ def test_inpaint_workload1_f32(method, dtype):
         dtype=dtype)
     got = u.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(got - ref)) <= 2e-4
+    if dtype == "f32_f64u":
+        ref32, _, _ = O.inpaint(method, f32.astype(np.float64), mask, p["sigma"], p["lam"], p["cycle_len"],
+                                p["max_cycles"])
+        assert np.max(np.abs(got - ref32)) <= 2e-6
     assert abs(_psnr(got, img) - _psnr(ref, img)) <= 0.01
     k = mask != 0
     np.testing.assert_array_equal(u.cpu().numpy()[k], f32[k])
@@ -304,8 +310,8 @@ def test_fullsize_2048_one_cycle_f32_vs_oracle(method):
 def test_fullsize_2048_bench_solve_against_the_oracle():
     """The benchmarked solve itself (2048 x 2048 phantom, sigma 1.5, lambda 0.02, 100
     FSI cycles of 40 = 4000 steps) against the FP64 oracle run to the same iterate:
-    FP32 within 2e-4 and 0.01 dB of PSNR, FP32 storage with the FP64 update within
-    2e-4, the FP64 GPU solve within 1e-10; Dirichlet pixels bitwise f. The oracle
+    FP32 within 2e-4 and 0.01 dB of PSNR, FP32 storage with the two-float FSI
+    update within 2e-6, the FP64 GPU solve within 1e-10; Dirichlet pixels bitwise f. The oracle
     takes about three minutes on 16 host cores."""
     img, mask, p = synth.workload(3)
     f32 = img.astype(np.float32)
@@ -324,7 +330,7 @@ def test_fullsize_2048_bench_solve_against_the_oracle():
     assert np.isfinite(a).all()
     assert np.max(np.abs(a - ref)) <= 2e-4
     assert abs(_psnr(a, img) - _psnr(ref, img)) <= 0.01
-    assert np.max(np.abs(umx.cpu().numpy().astype(np.float64) - ref)) <= 2e-4
+    assert np.max(np.abs(umx.cpu().numpy().astype(np.float64) - ref)) <= 2e-6
     assert np.max(np.abs(u64.cpu().numpy() - ref)) <= 1e-10
 
 
