@@ -187,6 +187,8 @@ size_t foeed_vjp_workspace_bytes(int w, int h, foeed_dtype dtype, const foeed_pa
  * the exact derivative of the discrete solve of foeed_inpaint: the forward
  * FSI solve is re-run with a checkpoint of (u^k, u^{k-1}) every
  * checkpoint_every steps, then each segment is recomputed from its checkpoint
+ * (checkpoint_every = 1: the forward steps write every state u^0 .. u^S into the
+ * workspace, (S + 1) images, and nothing is recomputed or copied)
  * and traversed backwards with the adjoint step kernels.
  *   grad_u  [h x pitch] dL/du_final (device)
  *   grad_f  [h x pitch] out: dL/df on the known pixels, 0 elsewhere; includes

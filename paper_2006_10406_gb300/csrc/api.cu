@@ -756,8 +756,14 @@ VjpLayout vjp_layout(int w, int h, foeed_dtype d, const foeed_params &p, int K)
     V.K = K;
     V.ncp = (int)((S + K - 1) / K);
     size_t off = V.base.total;
-    V.cp = off; off += V.img * 2 * (size_t)V.ncp;  // (u^s, u^{s-1}) at s = 0, K, 2K, ...
-    V.seg = off; off += V.img * (size_t)K;           // states of one segment
+    if (K == 1) {
+        // every state u^0 .. u^S, written by the forward steps themselves
+        V.cp = off; off += V.img * (size_t)(S + 1);
+        V.seg = off;
+    } else {
+        V.cp = off; off += V.img * 2 * (size_t)V.ncp;  // (u^s, u^{s-1}) at s = 0, K, 2K, ...
+        V.seg = off; off += V.img * (size_t)K;           // states of one segment
+    }
     V.g = off; off += V.img;
     V.pend = off; off += V.img;
     V.pv = off; off += V.img;
@@ -863,9 +869,22 @@ foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, voi
         return launch_step(false, d, &c, p, s);
     };
 
+    if (K == 1) {
+        // forward solve into the state history: step s reads u^s (and u^{s-1}, or u^s
+        // again at the first step of a cycle) and writes u^{s+1}; nothing is copied
+        T *hist = img(V.cp, 0);
+        CK(cudaMemcpyAsync(hist, buf[0], ibytes, cudaMemcpyDeviceToDevice, s));
+        for (long st = 0; st < S; ++st) {
+            const int k = (int)(st % n);
+            const T *cur = img(V.cp, st);
+            CK(fwd_step(k == 0 ? cur : img(V.cp, st - 1), cur, img(V.cp, st + 1), st));
+        }
+        if (u_out)
+            pitch_copy_kernel<T><<<g1, kRedThreads, 0, s>>>(img(V.cp, S), P, static_cast<T *>(u_out), pitch, w, h);
+    }
     // forward solve with checkpoints of (u^s, u^{s-1}) every K steps
     int icur = 0, iprev = 0;
-    for (long st = 0; st < S; ++st) {
+    for (long st = 0; st < S && K > 1; ++st) {
         const int k = (int)(st % n);
         if (k == 0) iprev = icur;
         if (st % K == 0) {
@@ -878,7 +897,7 @@ foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, voi
         iprev = icur;
         icur = inext;
     }
-    if (u_out)
+    if (u_out && K > 1)
         pitch_copy_kernel<T><<<g1, kRedThreads, 0, s>>>(buf[icur], P, static_cast<T *>(u_out), pitch, w, h);
 
     // backward: g = dL/du_final, then the segments in reverse
@@ -894,7 +913,14 @@ foeed_status run_vjp(const void *f, const uint8_t *mask, const void *grad_u, voi
     a.l2 = T(p.lambda * p.lambda);
     a.inv_l2 = T(1.0 / (p.lambda * p.lambda));
     gauss_taps<T>(p.sigma, a.wts);
-    for (int seg = V.ncp - 1; seg >= 0; --seg) {
+    for (long st = S - 1; st >= 0 && K == 1; --st) {  // every state is kept: no recomputation
+        const int k = (int)(st % n);
+        a.x = img(V.cp, st);
+        a.alpha = T((4.0 * k + 2.0) / (2.0 * k + 3.0));
+        a.first_of_cycle = k == 0;
+        CK(launch_adjoint<T>(&a, R, s));
+    }
+    for (int seg = V.ncp - 1; seg >= 0 && K > 1; --seg) {
         const long s0 = (long)seg * K, s1 = std::min<long>(S, s0 + K);
         // states u^{s0} .. u^{s1-1} of this segment, recomputed from its checkpoint
         CK(cudaMemcpyAsync(img(V.seg, 0), img(V.cp, 2 * seg), ibytes, cudaMemcpyDeviceToDevice, s));
