@@ -81,6 +81,14 @@ __device__ __forceinline__ void adj_cp_wait()
 {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
+
+// Eight consecutive floats from shared memory (two float4 loads; s is 16-byte aligned).
+__device__ __forceinline__ void ld_8f(const float *s, float *o)
+{
+    const float4 a = *reinterpret_cast<const float4 *>(s);
+    const float4 b = *reinterpret_cast<const float4 *>(s + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
 // B1: P(x) v and q at every pixel of a TW x 16 tile.
 template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
@@ -314,6 +322,269 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// B1 for FP32, register-blocked like the forward step kernel: 64 x 16 tiles,
+// 256 threads; the windows are copied with one fixed float4 column per thread,
+// the x pass produces 8 outputs per item, the y pass 2 rows per item, and the
+// tensor stage 4 consecutive positions per item from float4 shared loads.
+
+// The adjoint arithmetic of one position (the same operations as adj_b1_kernel's
+// FP32 branch): T_w = D : W and, when want_q, q = d/d(grad u_sigma) of W : D : H.
+__device__ __forceinline__ void adj_position_f32(const float gx, const float gy, const float hxx, const float hyy,
+                                                 const float hxy, const float wxx, const float wyy, const float wxy,
+                                                 const float inv_l2, const float l2, const bool want_q, float &txx,
+                                                 float &txy, float &tyy, float &qx, float &qy)
+{
+    const float rho2 = gx * gx + gy * gy;
+    const float t = fmaf(rho2, inv_l2, 1.f);
+    const float mu1 = adj_rsqrt(t);
+    const float sq = t * mu1;  // 1 / mu1
+    const float mu3 = adj_sqrt(mu1);
+    float C = 1.f, S = 0.f;
+    if (rho2 != 0.f) {
+        const float inv = adj_rcp(rho2);
+        C = (gx * gx - gy * gy) * inv;
+        S = 2.f * gx * gy * inv;
+    }
+    const float Ah = (hxx + hyy) * 0.5f, Bh = (hxx - hyy) * 0.5f;
+    const float Aw = (wxx + wyy) * 0.5f, Bw = (wxx - wyy) * 0.5f;
+    const float h11 = Ah + C * Bh + S * hxy, h22 = Ah - C * Bh - S * hxy, h12 = C * hxy - S * Bh;
+    const float w11 = Aw + C * Bw + S * wxy, w22 = Aw - C * Bw - S * wxy, w12 = C * wxy - S * Bw;
+    const float pp = mu1 * w11, qq = w22, rr = mu3 * w12;
+    const float hs = (pp + qq) * 0.5f, hd = (pp - qq) * 0.5f;
+    txx = hs + C * hd - S * rr;
+    txy = S * hd + C * rr;
+    tyy = hs - C * hd + S * rr;
+    if (want_q) {
+        // sq = 1/mu1 and mu3 = sqrt(mu1), so sqrt(sq) = 1/mu3 = mu3 sq; the two
+        // reciprocals share one: with A = l2 (sq + 1) and B = rs (rs + 1),
+        // 1/(A sq) = B / (A sq B) and 1/(A B) = sq / (A sq B)
+        const float dmu1 = -mu1 * mu1 * mu1 * (0.5f * inv_l2);
+        const float rs = mu3 * sq;
+        const float dmu3 = dmu1 * 0.5f * rs;
+        const float A = l2 * (sq + 1.f), B = rs * (rs + 1.f);
+        const float rAB = adj_rcp(A * sq * B);
+        const float c1 = B * rAB;
+        const float c3 = sq * rAB;
+        const float srho = dmu1 * w11 * h11 + 2.f * dmu3 * w12 * h12;
+        const float th = -c1 * 2.f * (w12 * h11 + w11 * h12) - 2.f * c3 * (-(w11 - w22) * h12 - w12 * (h11 - h22));
+        qx = 2.f * gx * srho - gy * th;
+        qy = 2.f * gy * srho + gx * th;
+    }
+}
+
+template <int R>
+struct AdjFast {
+    static constexpr int TW = 64, TH = kAdjTH, HL = R + 2;
+    static constexpr int XS = 84, XH = TH + 2 * HL;  // x window: cols x0-8 .. x0+71 (80 loaded), stride 21 float4
+    static constexpr int VS = 76, VH = TH + 4;       // v window: cols x0-4 .. x0+67 (72 loaded), rows tile +- 2
+    static constexpr int MS = 72;                   // mask window stride (bytes)
+    static constexpr int PS = 76;                   // x pass: cols x0-2 .. x0+69 (72 computed), XH rows
+    static constexpr int SS = 76, SH = TH + 4;      // u_sigma: cols x0-2 .. x0+65 (68), rows tile +- 2
+    static constexpr int QS = 68, QH = TH + 2;      // T_w planes: positions tile +- 1, cols x0-1 .. x0+66
+    static constexpr int PQ = (PS * XH > 3 * QS * QH) ? PS * XH : 3 * QS * QH;  // x pass and T_w share
+    static constexpr int ELEMS = XS * XH + VS * VH + PQ + SS * SH + (MS * VH) / 4;
+    static constexpr size_t SMEM = sizeof(float) * ELEMS;
+};
+
+template <int R>
+__global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
+{
+    using G = AdjFast<R>;
+    constexpr int TW = G::TW, TH = G::TH, HL = G::HL;
+    extern __shared__ __align__(16) float sm[];
+    float *sxw = sm;                       // x window
+    float *sv = sxw + G::XS * G::XH;       // g, then v = (1 - M) g
+    float *sxp = sv + G::VS * G::VH;       // x pass; then the T_w planes
+    float *tw = sxp;
+    float *ss = sxp + G::PQ;               // u_sigma
+    unsigned char *smk = reinterpret_cast<unsigned char *>(ss + G::SS * G::SH);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int w = a.w, h = a.h;
+    const long pitch = a.pitch;
+
+    // ---- windows: thread tid owns one float4 (or 4-byte) column and strided rows ----
+    {
+        const bool xin = x0 - 8 >= 0 && x0 + 72 <= w;
+        const bool vin = x0 - 4 >= 0 && x0 + 68 <= w;
+        if (tid < 240) {  // x: 20 float4 columns, 12 rows per pass
+            const int q = tid % 20, r0 = tid / 20, gx = x0 - 8 + 4 * q;
+            uint32_t d = adj_smem(sxw) + 4u * (uint32_t)(r0 * G::XS + 4 * q);
+            for (int r = r0; r < G::XH; r += 12, d += 4u * 12 * G::XS) {
+                const float *row = a.x + (long)mirror_idx(y0 - HL + r, h) * pitch;
+                if (xin) adj_cp16(d, row + gx);
+                else
+                    for (int j = 0; j < 4; ++j) adj_cp_elem(d + 4u * j, row + mirror_idx(gx + j, w));
+            }
+        }
+        if (tid < 252) {  // g: 18 float4 columns, 14 rows per pass; mask: 18 four-byte columns
+            const int q = tid % 18, r0 = tid / 18, gx = x0 - 4 + 4 * q;
+            uint32_t d = adj_smem(sv) + 4u * (uint32_t)(r0 * G::VS + 4 * q);
+            uint32_t dm = adj_smem(smk) + (uint32_t)(r0 * G::MS + 4 * q);
+            for (int r = r0; r < G::VH; r += 14, d += 4u * 14 * G::VS, dm += 14 * G::MS) {
+                const long ro = (long)mirror_idx(y0 - 2 + r, h) * pitch;
+                if (vin) {
+                    adj_cp16(d, a.g + ro + gx);
+                    adj_cp4(dm, a.mask + ro + gx);
+                } else {
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = mirror_idx(gx + j, w);
+                        adj_cp_elem(d + 4u * j, a.g + ro + c);
+                        smk[(r * G::MS + 4 * q) + j] = a.mask[ro + c];
+                    }
+                }
+            }
+        }
+        adj_cp_wait();
+    }
+    __syncthreads();
+    // v = (1 - M) g, one float4 per item
+    for (int i = tid; i < G::VH * 18; i += 256) {
+        const int r = i / 18, q = i - r * 18;
+        float4 *p = reinterpret_cast<float4 *>(sv + r * G::VS + 4 * q);
+        const uint32_t m = *reinterpret_cast<const uint32_t *>(smk + r * G::MS + 4 * q);
+        if (m) {
+            float4 v = *p;
+            if (m & 0xffu) v.x = 0.f;
+            if (m & 0xff00u) v.y = 0.f;
+            if (m & 0xff0000u) v.z = 0.f;
+            if (m & 0xff000000u) v.w = 0.f;
+            *p = v;
+        }
+    }
+    // ---- x pass: sxp (row i, col c <-> global x0-2+c) <- x window cols c+6-R .. c+6+R; 8 outputs per item ----
+    {
+        float wt[2 * R + 1];
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) wt[t] = a.wts[t];
+        for (int i = tid; i < G::XH * 9; i += 256) {
+            const int g = i / G::XH, r = i - g * G::XH;  // consecutive lanes on consecutive rows
+            const float *src = sxw + r * G::XS + 8 * g;
+            float v[20];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const float4 f = *reinterpret_cast<const float4 *>(src + 4 * j);
+                v[4 * j] = f.x; v[4 * j + 1] = f.y; v[4 * j + 2] = f.z; v[4 * j + 3] = f.w;
+            }
+            float o[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = -R; t <= R; ++t) acc = fmaf(wt[t + R], v[6 + k + t], acc);
+                o[k] = acc;
+            }
+            float *dst = sxp + r * G::PS + 8 * g;
+            *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
+    __syncthreads();
+    // ---- y pass: ss row i (global y0-2+i) <- sxp rows i .. i+2R; 2 rows x 4 columns per item ----
+    {
+        float wt[2 * R + 1];
+#pragma unroll
+        for (int t = 0; t <= 2 * R; ++t) wt[t] = a.wts[t];
+        constexpr int NS = G::SH / 2;
+        for (int i = tid; i < NS * 17; i += 256) {
+            const bool main = i < NS * 16;
+            const int s = main ? (i >> 4) : i - NS * 16, q = main ? (i & 15) : 16;
+            const float *src = sxp + (2 * s) * G::PS + 4 * q;
+            float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+#pragma unroll
+            for (int j = 0; j < 2 * R + 2; ++j) {
+                const float4 f = *reinterpret_cast<const float4 *>(src + j * G::PS);
+                if (j <= 2 * R) {
+                    const float c = wt[j];
+                    o0.x = fmaf(c, f.x, o0.x); o0.y = fmaf(c, f.y, o0.y); o0.z = fmaf(c, f.z, o0.z); o0.w = fmaf(c, f.w, o0.w);
+                }
+                if (j >= 1) {
+                    const float c = wt[j - 1];
+                    o1.x = fmaf(c, f.x, o1.x); o1.y = fmaf(c, f.y, o1.y); o1.z = fmaf(c, f.z, o1.z); o1.w = fmaf(c, f.w, o1.w);
+                }
+            }
+            *reinterpret_cast<float4 *>(ss + (2 * s) * G::SS + 4 * q) = o0;
+            *reinterpret_cast<float4 *>(ss + (2 * s + 1) * G::SS + 4 * q) = o1;
+        }
+    }
+    __syncthreads();
+    // ---- T_w and q at positions (r, c), r = 0 .. TH+1, c = 0 .. 67 <-> global (y0-1+r, x0-1+c);
+    // one row of four positions per item ----
+    constexpr int PL = G::QS * G::QH;
+    {
+        const float l2 = a.l2, inv_l2 = a.inv_l2;
+        for (int i = tid; i < G::QH * 17; i += 256) {
+            const bool main = i < G::QH * 16;
+            const int q = main ? (i & 15) : 16, r = main ? (i >> 4) : i - G::QH * 16;
+            float su[8], sc[8], sd[8], xu[8], xc[8], xd[8], vu[8], vc[8], vd[8];
+            // u_sigma rows r .. r+2, cols 4q .. 4q+7 (position 4q+k at index k+1)
+            const float *sp = ss + r * G::SS + 4 * q;
+            // x rows (r-1+HL) -1 .. +1, cols 4q+4 .. 4q+11 of the window (position at index k+3)
+            const float *xp = sxw + (r - 2 + HL) * G::XS + 4 * q + 4;
+            // v rows r .. r+2, cols 4q .. 4q+7 of the v window (position at index k+3)
+            const float *vp = sv + r * G::VS + 4 * q;
+            ld_8f(sp, su); ld_8f(sp + G::SS, sc); ld_8f(sp + 2 * G::SS, sd);
+            ld_8f(xp, xu); ld_8f(xp + G::XS, xc); ld_8f(xp + 2 * G::XS, xd);
+            ld_8f(vp, vu); ld_8f(vp + G::VS, vc); ld_8f(vp + 2 * G::VS, vd);
+            float o0[4], o1[4], o2[4];
+            const int gyp = y0 + r - 1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float gx = (sc[k + 2] - sc[k]) * 0.5f, gy = (sd[k + 1] - su[k + 1]) * 0.5f;
+                const float hxx = (xc[k + 2] + xc[k + 4]) - 2.f * xc[k + 3];
+                const float hyy = (xu[k + 3] + xd[k + 3]) - 2.f * xc[k + 3];
+                const float hxy = ((xd[k + 4] + xu[k + 2]) - (xd[k + 2] + xu[k + 4])) * 0.25f;
+                const float wxx = (vc[k + 2] + vc[k + 4]) - 2.f * vc[k + 3];
+                const float wyy = (vu[k + 3] + vd[k + 3]) - 2.f * vc[k + 3];
+                const float wxy = ((vd[k + 4] + vu[k + 2]) - (vd[k + 2] + vu[k + 4])) * 0.25f;
+                const int c = 4 * q + k, gxp = x0 + c - 1;
+                const bool want_q = r >= 1 && r <= TH && c >= 1 && c <= TW && gxp < w && gyp < h;
+                float qx = 0.f, qy = 0.f;
+                adj_position_f32(gx, gy, hxx, hyy, hxy, wxx, wyy, wxy, inv_l2, l2, want_q, o0[k], o1[k], o2[k], qx, qy);
+                if (want_q) {
+                    const long gi = (long)gyp * pitch + gxp;
+                    a.qx[gi] = qx;
+                    a.qy[gi] = qy;
+                }
+            }
+            float *dst = tw + r * G::QS + 4 * q;
+            *reinterpret_cast<float4 *>(dst) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+            *reinterpret_cast<float4 *>(dst + PL) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+            *reinterpret_cast<float4 *>(dst + 2 * PL) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+        }
+    }
+    __syncthreads();
+    // ---- P(x) v: outer divergence of T_w at the tile's pixels, 4 per thread ----
+    {
+        const int qe = tid & 15, ty = tid >> 4;  // output row ty, cols 4qe .. 4qe+3 <-> positions (ty+1, 4qe+1+k)
+        const int gyp = y0 + ty, gxp = x0 + 4 * qe;
+        if (gyp < h && gxp < w) {
+            float xx[8], yu[8], yc[8], yd[8], du[8], dd[8];
+            const float *t0 = tw + (ty + 1) * G::QS + 4 * qe;
+            ld_8f(t0, xx);
+            ld_8f(t0 + 2 * PL - G::QS, yu); ld_8f(t0 + 2 * PL, yc); ld_8f(t0 + 2 * PL + G::QS, yd);
+            ld_8f(t0 + PL - G::QS, du); ld_8f(t0 + PL + G::QS, dd);
+            float o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = 1 + k;
+                const float dxx = (xx[c - 1] + xx[c + 1]) - 2.f * xx[c];
+                const float dyy = (yu[c] + yd[c]) - 2.f * yc[c];
+                const float dxy = ((dd[c + 1] + du[c - 1]) - (dd[c - 1] + du[c + 1])) * 0.5f;
+                o[k] = (dxx + dyy) + dxy;
+            }
+            const long gi = (long)gyp * pitch + gxp;
+            if (gxp + 3 < w) {
+                *reinterpret_cast<float4 *>(a.pv + gi) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (gxp + k < w) a.pv[gi + k] = o[k];
+            }
+        }
+    }
+}
+
 template <typename T, int R>
 struct AdjSmem {
     static constexpr int HL = R + 2, TW = adj_tile_w<T>(), TH = kAdjTH;
@@ -332,10 +603,15 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
         cudaError_t e =
             cudaFuncSetAttribute(adj_b1_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(adj_b1_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjFast<R>::SMEM);
+        if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(adj_b2_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
     }
     dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
-    adj_b1_kernel<T, R, TW><<<grid, 256, SM::B1, s>>>(*ap);
+    if (sizeof(T) == sizeof(float))
+        adj_b1_fast<R><<<grid, 256, AdjFast<R>::SMEM, s>>>(*reinterpret_cast<const AdjArgs<float> *>(ap));
+    else
+        adj_b1_kernel<T, R, TW><<<grid, 256, SM::B1, s>>>(*ap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adj_b2_kernel<T, R, TW><<<grid, 256, SM::B2, s>>>(*ap);
