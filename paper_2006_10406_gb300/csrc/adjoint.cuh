@@ -282,9 +282,36 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
     T *sxp = sr + RW * RH;                    // x pass: RH rows x TW columns
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    for (int i = tid; i < RW * RH; i += 256) {
-        int r = i / RW, c = i - r * RW;
-        sr[i] = adj_divq(a, mirror_idx(x0 - R + c, a.w), mirror_idx(y0 - R + r, a.h));
+    // FP32 tiles whose q windows (rows tile-R-1 .. tile+TH+R, columns tile-8 ..
+    // tile+71) lie inside the image copy them to shared memory (16-byte cp.async,
+    // one fixed float4 column per thread) and take -D_odd q from there; the others
+    // read q through L1 with the odd ghosts at the border.
+    constexpr int QR = RH + 2, QC = 80;
+    const bool inner = sizeof(T) == sizeof(float) && x0 - 8 >= 0 && x0 + 72 <= a.w && y0 - R - 1 >= 0 &&
+                       y0 + TH + R + 1 <= a.h;
+    if (inner) {
+        float *sqx = reinterpret_cast<float *>(sxp + RH * TW), *sqy = sqx + QR * QC;
+        if (tid < 240) {
+            const int q = tid % 20, r0 = tid / 20;
+            for (int r = r0; r < QR; r += 12) {
+                const long go = (long)(y0 - R - 1 + r) * a.pitch + (x0 - 8 + 4 * q);
+                adj_cp16(adj_smem(sqx + r * QC + 4 * q), reinterpret_cast<const float *>(a.qx) + go);
+                adj_cp16(adj_smem(sqy + r * QC + 4 * q), reinterpret_cast<const float *>(a.qy) + go);
+            }
+        }
+        adj_cp_wait();
+        __syncthreads();
+        for (int i = tid; i < RW * RH; i += 256) {
+            // position (r, c) <-> pixel (y0-R+r, x0-R+c) <-> window row r+1, column c+8-R
+            const int r = i / RW, c = i - r * RW;
+            const float *px = sqx + (r + 1) * QC + (c + 8 - R), *py = sqy + (r + 1) * QC + (c + 8 - R);
+            sr[i] = T(-((px[1] - px[-1]) + (py[QC] - py[-QC])) * 0.5f);
+        }
+    } else {
+        for (int i = tid; i < RW * RH; i += 256) {
+            int r = i / RW, c = i - r * RW;
+            sr[i] = adj_divq(a, mirror_idx(x0 - R + c, a.w), mirror_idx(y0 - R + r, a.h));
+        }
     }
     __syncthreads();
     for (int i = tid; i < RH * TW; i += 256) {
@@ -591,7 +618,8 @@ struct AdjSmem {
     static constexpr size_t B1 = sizeof(T) * ((TW + 16) * (TH + 2 * HL) + (TW + 8) * (TH + 4) +
                                               (TH + 2 * HL) * (TW + 4) + (TW + 4) * (TH + 4) + 3 * (TW + 2) * (TH + 2)) +
                                  (size_t)(TW + 8) * (TH + 4);
-    static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW);
+    static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW) +
+                                 (sizeof(T) == sizeof(float) ? sizeof(float) * 2 * (TH + 2 * R + 2) * 80 : 0);
 };
 
 template <typename T, int R>
