@@ -292,23 +292,24 @@ def convergence_leg(fg, synth, torch, dev, stream):
     return {"workload": p["name"], "tol": p["tol"], "cycle_len": p["cycle_len"], **out}
 
 
-def gradient_once(fg, synth, torch, dev, rank):
-    """One warm-up and one timed gradient of the W5 workload (checkpoint every 16 steps)."""
+def gradient_once(fg, synth, torch, dev, rank, checkpoint_every=16):
+    """One warm-up and one timed gradient of the W5 workload (a checkpoint every
+    `checkpoint_every` steps; 1 keeps every state)."""
     import numpy as np
     img, mask, p = synth.workload(5)
     f = torch.from_numpy(img.astype(np.float32)).to(dev)
     m = torch.from_numpy(mask).to(dev)
     g = torch.full_like(f, 1e-3)
     args = (f, m, g, p["lam"], p["sigma"], p["cycle_len"], p["max_cycles"])
-    fg.foeed_inpaint_vjp(*args, checkpoint_every=16)
+    fg.foeed_inpaint_vjp(*args, checkpoint_every=checkpoint_every)
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    gf, _ = fg.foeed_inpaint_vjp(*args, checkpoint_every=16)
+    gf, _ = fg.foeed_inpaint_vjp(*args, checkpoint_every=checkpoint_every)
     b.record()
     torch.cuda.synchronize(dev)
     if rank == 0:
-        print(json.dumps({"gradient_ms": a.elapsed_time(b), "workload": p["name"],
+        print(json.dumps({"gradient_ms": a.elapsed_time(b), "workload": p["name"], "checkpoint_every": checkpoint_every,
                           "grad_norm": float(gf.norm())}), flush=True)
 
 
@@ -393,6 +394,8 @@ def main():
                          "shape the benchmark uses")
     ap.add_argument("--minimal", action="store_true",
                     help="only the warm-up and timed solves (for profiler launch lists)")
+    ap.add_argument("--checkpoint-every", type=int, default=16,
+                    help="checkpoint interval of --gradient-only (1: every state kept, nothing recomputed)")
     ap.add_argument("--gradient-only", action="store_true",
                     help="only one warm-up and one timed gradient of the 1024^2 tonal-optimisation "
                          "workload (for profiler launch lists of the backward kernels)")
@@ -411,7 +414,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if args.gradient_only:
-        return gradient_once(fg, synth, torch, dev, rank)
+        return gradient_once(fg, synth, torch, dev, rank, args.checkpoint_every)
     pg = None
     if world > 1:
         import torch.distributed as dist
