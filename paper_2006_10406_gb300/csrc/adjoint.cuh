@@ -433,10 +433,9 @@ __global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
 
     // ---- windows: thread tid owns one float4 (or 4-byte) column and strided rows ----
     {
-        const bool xin = x0 - 8 >= 0 && x0 + 72 <= w;
-        const bool vin = x0 - 4 >= 0 && x0 + 68 <= w;
         if (tid < 240) {  // x: 20 float4 columns, 12 rows per pass
             const int q = tid % 20, r0 = tid / 20, gx = x0 - 8 + 4 * q;
+            const bool xin = gx >= 0 && gx + 4 <= w;  // this column lies inside the image
             uint32_t d = adj_smem(sxw) + 4u * (uint32_t)(r0 * G::XS + 4 * q);
             for (int r = r0; r < G::XH; r += 12, d += 4u * 12 * G::XS) {
                 const float *row = a.x + (long)mirror_idx(y0 - HL + r, h) * pitch;
@@ -447,6 +446,7 @@ __global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
         }
         if (tid < 252) {  // g: 18 float4 columns, 14 rows per pass; mask: 18 four-byte columns
             const int q = tid % 18, r0 = tid / 18, gx = x0 - 4 + 4 * q;
+            const bool vin = gx >= 0 && gx + 4 <= w;
             uint32_t d = adj_smem(sv) + 4u * (uint32_t)(r0 * G::VS + 4 * q);
             uint32_t dm = adj_smem(smk) + (uint32_t)(r0 * G::MS + 4 * q);
             for (int r = r0; r < G::VH; r += 14, d += 4u * 14 * G::VS, dm += 14 * G::MS) {

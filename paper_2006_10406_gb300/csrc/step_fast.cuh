@@ -240,9 +240,12 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                                      "l"(src + step * k)
                                      : "memory");
             } else {
+                // border tiles: rows are mirrored; a float4 column inside the image is still
+                // one 16-byte copy, only columns reaching past the border go element-wise
+                const bool cin = gx >= 0 && gx + 4 <= w;
                 for (int r = r0; r < G::SU_H; r += RP, sa += 4u * RP * G::SU_W) {
                     const float *row = uc + (long)mirror_idx(y0 - G::HL + r, h) * pitch;
-                    if (xin) {
+                    if (cin) {
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(row + gx) : "memory");
                     } else {
 #pragma unroll
