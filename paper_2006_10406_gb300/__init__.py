@@ -59,10 +59,10 @@ class _Report(C.Structure):
 
 class _TilePlan(C.Structure):
     _fields_ = [("tile_h", C.c_int), ("images", C.c_int), ("images_h16", C.c_int), ("tuned", C.c_int),
-                ("us_h32", C.c_float), ("us_h16", C.c_float), ("us_chosen", C.c_float)]
+                ("us_h32", C.c_float), ("us_h16", C.c_float), ("us_chosen", C.c_float), ("us_h64", C.c_float)]
 
 
-TILE_POLICY = {"auto": 0, "h16": 16, "h32": 32, 0: 0, 16: 16, 32: 32}
+TILE_POLICY = {"auto": 0, "h16": 16, "h32": 32, "h64": 64, 0: 0, 16: 16, 32: 32, 64: 64}
 
 
 @dataclass
@@ -174,8 +174,9 @@ def _as_device_image(a, dtype, device):
 
 def set_tile_policy(policy="auto"):
     """Tile shape of the register-blocked FP32 kernels for later calls on this host
-    thread: "auto" (timed once per size and kept), "h32" or "h16" (64 x 32 or 64 x 16
-    tiles for every image). Results are bitwise the same under every policy."""
+    thread: "auto" (timed once per size and kept), "h64", "h32" or "h16" (64 x 64,
+    64 x 32 or 64 x 16 tiles; 64 x 64 for single FOEED images only). Results are
+    bitwise the same under every policy."""
     _check(lib().foeed_set_tile_policy(TILE_POLICY[policy]))
 
 

@@ -338,7 +338,7 @@ struct TuneKey {
 
 struct TuneVal {
     int choice;  // single image: tile height; batch: tile-count threshold of the 64 x 16 images
-    float us_h32, us_h16, us_chosen;
+    float us_h32, us_h16, us_h64, us_chosen;
 };
 
 std::mutex g_tune_mu;
@@ -393,7 +393,7 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
     *tile_h = 0;
     if (d == FOEED_F64 || !fast_params(eed, p)) return FOEED_OK;
     if (g_tile_policy != FOEED_TILES_AUTO) {
-        *tile_h = g_tile_policy;
+        *tile_h = (eed && g_tile_policy == FOEED_TILES_H64) ? 32 : g_tile_policy;
     } else {
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -416,17 +416,19 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
             CK(launch_step(eed, d, nullptr, p, s));
             cudaStream_t cs = nullptr;
             CK(capture_stream(dev, &cs));
-            const int th[2] = {32, 16};
-            cudaGraphExec_t ex[2] = {nullptr, nullptr};
+            // candidates: 64 x 32 and 64 x 16 tiles, and 64 x 64 for FOEED
+            const int th[3] = {32, 16, 64};
+            const int ncand = eed ? 2 : 3;
+            cudaGraphExec_t ex[3] = {nullptr, nullptr, nullptr};
             struct ExecGuard {
                 cudaGraphExec_t *e;
                 ~ExecGuard()
                 {
-                    for (int i = 0; i < 2; ++i)
+                    for (int i = 0; i < 3; ++i)
                         if (e[i]) cudaGraphExecDestroy(e[i]);
                 }
             } guard{ex};
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < ncand; ++i) {
                 CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
                 cudaError_t err = cudaSuccess;
                 for (int k = 0; k < kTuneSteps && err == cudaSuccess; ++k) {
@@ -442,24 +444,29 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
                 if (err != cudaSuccess) return fail(FOEED_ERR_CUDA, "capturing the tile-shape timing: %s",
                                                     cudaGetErrorString(err));
             }
-            float us[2] = {-1.f, -1.f};
+            float us[3] = {-1.f, -1.f, -1.f};
             // the candidates alternate over kTuneRounds rounds and each keeps its
-            // fastest time, so a clock still ramping up favours neither
+            // fastest time, so a clock still ramping up favours none
             for (int round = 0; round < kTuneRounds; ++round)
-                for (int i = 0; i < 2; ++i) {
+                for (int i = 0; i < ncand; ++i) {
                     const float t = time_launches([&] { return cudaGraphLaunch(ex[i], s); }, s, 2) / kTuneSteps;
                     if (t < 0.f)
                         return fail(FOEED_ERR_CUDA, "timing the tile shapes: %s", cudaGetErrorString(cudaGetLastError()));
                     if (us[i] < 0.f || t < us[i]) us[i] = t;
                 }
-            v.choice = us[1] < us[0] ? 16 : 32;
+            int best = 0;
+            for (int i = 1; i < ncand; ++i)
+                if (us[i] < us[best]) best = i;
+            v.choice = th[best];
             v.us_h32 = us[0];
             v.us_h16 = us[1];
-            v.us_chosen = us[1] < us[0] ? us[1] : us[0];
+            v.us_h64 = ncand > 2 ? us[2] : 0.f;
+            v.us_chosen = us[best];
             tune_store(k, v);
             g_last_plan.tuned = 1;
             g_last_plan.us_h32 = v.us_h32;
             g_last_plan.us_h16 = v.us_h16;
+            g_last_plan.us_h64 = v.us_h64;
             g_last_plan.us_chosen = v.us_chosen;
             *tile_h = v.choice;
         }
@@ -763,7 +770,8 @@ foeed_status foeed_apply_tensor_field(const void *u, const void *d, void *Pu, in
 
 foeed_status foeed_set_tile_policy(int policy)
 {
-    if (policy != FOEED_TILES_AUTO && policy != FOEED_TILES_H16 && policy != FOEED_TILES_H32)
+    if (policy != FOEED_TILES_AUTO && policy != FOEED_TILES_H16 && policy != FOEED_TILES_H32 &&
+        policy != FOEED_TILES_H64)
         return fail(FOEED_ERR_ARG, "unknown tile policy %d", policy);
     g_tile_policy = policy;
     return FOEED_OK;
@@ -1184,7 +1192,7 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     };
     g_last_plan = foeed_tile_plan{};
     g_last_plan.images = count;
-    int thresh = g_tile_policy == FOEED_TILES_H16 ? INT_MAX : 0;
+    int thresh = g_tile_policy == FOEED_TILES_H16 ? INT_MAX : 0;  // a batch has no 64 x 64 tiles
     if (g_tile_policy == FOEED_TILES_AUTO) {
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -1223,7 +1231,7 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
                     if (tc[ci] < 0.f || us < tc[ci]) tc[ci] = us;
                 }
             float best = -1.f;
-            v.us_h32 = v.us_h16 = 0.f;
+            v.us_h32 = v.us_h16 = v.us_h64 = 0.f;
             for (size_t ci = 0; ci < cand.size(); ++ci) {
                 if (cand[ci] == 0) v.us_h32 = tc[ci];
                 if (cand[ci] == INT_MAX) v.us_h16 = tc[ci];

@@ -165,7 +165,8 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
 template <int R, bool EED, int TH_ = 32>
 struct FastTile {
     static constexpr int TW = 64, TH = TH_;
-    static_assert(TH == 32 || TH == 16, "tile height");
+    static_assert(TH == 64 || TH == 32 || TH == 16, "tile height");
+    static constexpr int NTHR = TH == 64 ? 512 : 256;    // threads per CTA
     static constexpr int HL = R + 2;
     static constexpr int SU_W = 84, SU_H = TH + 2 * HL;  // u: columns tile-8 .. tile+75
     // Row strides are an odd number of float4 so that the column-major stages
@@ -179,12 +180,12 @@ struct FastTile {
     static constexpr int ELEMS = SU_W * SU_H + SXT + SS_W * SS_H;
     static constexpr size_t SMEM = sizeof(float) * ELEMS;
     // y pass: strips of RS rows; tensor stage: N3 segments of 3 rows, then N2 of 2
-    static constexpr int RS = SS_H % 6 == 0 ? 6 : 5;
+    static constexpr int RS = SS_H % 6 == 0 ? 6 : (SS_H % 5 == 0 ? 5 : 4);
     static_assert(SS_H % RS == 0, "strip height");
     static constexpr int N2 = ST_H % 3 == 0 ? 0 : (ST_H % 3 == 1 ? 2 : 1);
     static constexpr int N3 = (ST_H - 2 * N2) / 3;
     // output stage: ER rows per thread (16 four-pixel groups per row, 256 threads)
-    static constexpr int ER = TH * (TW / 4) / 256;
+    static constexpr int ER = TH * (TW / 4) / NTHR;
 };
 
 // The image one tile belongs to: its buffers for this step and its geometry.
@@ -224,7 +225,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         const bool xin = (x0 - 8 >= 0) && (x0 + 76 <= w);
         const bool yin = (y0 - G::HL >= 0) && (y0 + G::TH + G::HL <= h);
         constexpr int NQ = G::SU_W / 4;                // 21 float4 per row
-        constexpr int RP = 256 / NQ;                   // 12 rows per pass
+        constexpr int RP = G::NTHR / NQ;                 // rows per pass (12, or 24 with 512 threads)
         constexpr int NP = (G::SU_H + RP - 1) / RP;    // passes
         if (tid < RP * NQ) {
             const int q = tid % NQ, r0 = tid / NQ;
@@ -267,7 +268,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
 #pragma unroll
         for (int t = 0; t <= 2 * R; ++t) wt[t] = p.wts[t];
         constexpr int NG = 9;  // 8-wide output groups per row (columns tile-2 .. tile+69)
-        for (int i = tid; i < G::SX_H * NG; i += 256) {
+        for (int i = tid; i < G::SX_H * NG; i += G::NTHR) {
             const int g = i / G::SX_H, r = i - g * G::SX_H;  // consecutive lanes on consecutive rows
             const float *src = su + r * G::SU_W + 8 * g;
             float v[20];
@@ -300,7 +301,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         constexpr int NQ = 17;             // groups per row (columns tile-2 .. tile+65)
         constexpr int NS = G::SS_H / RS;   // strips
         static_assert(NQ == 17, "16 column groups plus one");
-        for (int i = tid; i < NS * NQ; i += 256) {
+        for (int i = tid; i < NS * NQ; i += G::NTHR) {
             // lanes along the first 16 column groups of a strip (conflict-free quarter
             // warps); the strips of the 17th group come last
             const bool main = i < NS * 16;
@@ -339,7 +340,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         constexpr int NQ = G::ST_W / 4;  // 17
         static_assert(NQ == 17, "16 column groups plus one");
         constexpr int NSEG = G::N3 + G::N2;  // TH 32: ten segments of 3 rows, two of 2; TH 16: six of 3
-        for (int i = tid; i < NSEG * NQ; i += 256) {
+        for (int i = tid; i < NSEG * NQ; i += G::NTHR) {
             // lanes along the first 16 column groups of a segment (conflict-free quarter
             // warps); the segments of the 17th group come last
             const bool main = i < NSEG * 16;
@@ -371,7 +372,7 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     // barrier, so that their latency overlaps the wait.
     constexpr int NQE = G::TW / 4;  // 16 groups per row
     constexpr int ER = G::ER;       // rows per thread
-    static_assert(G::TH * NQE == 256 * ER, "whole output groups per thread");
+    static_assert(G::TH * NQE == G::NTHR * ER, "whole output groups per thread");
     const int qe = tid % NQE, re = ER * (tid / NQE);
     float4 pre_up[ER];
     uint32_t pre_mk[ER];
@@ -557,7 +558,7 @@ constexpr long long kFastSmallTiles = 304;
 
 // One FSI step over one image, one CTA per 64 x TH tile.
 template <int R, bool EED, typename U, int TH>
-__global__ void __launch_bounds__(256) fsi_step_fast(const StepArgs<float> p)
+__global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR) fsi_step_fast(const StepArgs<float> p)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[64];
@@ -644,9 +645,24 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
     if (!ap) {
         cudaError_t e = cudaFuncSetAttribute(k32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G32::SMEM);
         if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G16::SMEM);
+        e = cudaFuncSetAttribute(k16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G16::SMEM);
+        if constexpr (!EED) {
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(fsi_step_fast<R, EED, U, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)FastTile<R, EED, 64>::SMEM);
+        }
+        return e;
     }
     const int ntx = (ap->w + 63) / 64;
+    if constexpr (!EED) {
+        // 64 x 64 tiles, 512 threads, two CTAs per SM (FOEED only: EED's four T
+        // planes would not fit twice in an SM's shared memory)
+        if (ap->tile_h == 64) {
+            using G64 = FastTile<R, EED, 64>;
+            dim3 grid(ntx, (ap->h + 63) / 64);
+            return launch_step_kernel(fsi_step_fast<R, EED, U, 64>, grid, G64::NTHR, G64::SMEM, s, *ap);
+        }
+    }
     const bool h16 = ap->tile_h == 16 || (ap->tile_h != 32 && (long long)ntx * ((ap->h + 31) / 32) < kFastSmallTiles);
     if (h16) {
         dim3 grid(ntx, (ap->h + 15) / 16);

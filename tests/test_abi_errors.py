@@ -156,17 +156,17 @@ def test_messages_are_per_call():
 
 
 def test_tile_policy_arguments_are_checked_on_the_host():
-    """foeed_set_tile_policy accepts AUTO (0), 16 and 32 only; foeed_last_tile_plan
+    """foeed_set_tile_policy accepts AUTO (0), 16, 32 and 64 only; foeed_last_tile_plan
     rejects NULL. Neither touches the GPU."""
     import ctypes as C
 
     import paper_2006_10406_gb300 as fg
     L = fg.lib()
     try:
-        for bad in (1, 8, 64, -1):
+        for bad in (1, 8, 128, -1):
             assert L.foeed_set_tile_policy(bad) == 1
             assert b"tile policy" in L.foeed_last_error()
-        for good in (16, 32, 0):
+        for good in (16, 32, 64, 0):
             assert L.foeed_set_tile_policy(good) == 0
         assert L.foeed_last_tile_plan(None) == 1
         plan = fg._TilePlan()

@@ -427,6 +427,33 @@ def test_fast_and_generic_f32_paths_match_oracle(method, shape, sigma):
         np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
 
 
+@pytest.mark.parametrize("policy", ["h16", "h32", "h64"])
+@pytest.mark.parametrize("shape", [(100, 130), (630, 1030), (70, 64), (130, 200)])
+def test_fast_step_each_tile_shape_matches_oracle(policy, shape):
+    """One FOEED step on each fixed tile shape (64 x 16, 64 x 32, 64 x 64 tiles with
+    512 threads), ragged in both directions, inside a guard band."""
+    rng = _rng(400)
+    h, w = shape
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    uprev = (ucur + 0.01 * rng.normal(size=shape)).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.08).astype(np.uint8)
+    ref = O.fsi_step(0, uprev, ucur, mask, 1.5, 0.05, 1.5, 0.03)
+    pitch = ((w + 3) // 4) * 4 + 4
+    (a, ab), (b, bb) = _guarded(uprev, pitch, torch.float32), _guarded(ucur, pitch, torch.float32)
+    m, mb = _guarded(mask, pitch, torch.uint8)
+    out, ob = _guarded(np.zeros(shape), pitch, torch.float32)
+    try:
+        fg.set_tile_policy(policy)
+        fg.foeed_step(a, b, out, m, 1.5, 0.03, 1.5, tau=0.05)
+        torch.cuda.synchronize()
+    finally:
+        fg.set_tile_policy("auto")
+    assert all(_band_intact(x, w) for x in (ab, bb, mb, ob))
+    got = out.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-5)
+    np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
+
+
 @pytest.mark.parametrize("g_kind,mu3", [(1, 0), (2, 1), (0, 2), (0, 1)])
 def test_generic_f32_variants(g_kind, mu3):
     rng = _rng(300 + g_kind)
@@ -468,16 +495,18 @@ def test_autotuned_solve_equals_each_fixed_tile_shape(method, shape):
         fg.set_tile_policy("auto")
         ua, _ = solve(f, m, lam, sigma, 8, 3)
         plan = fg.last_tile_plan()
-        assert plan["images"] == 1 and plan["tile_h"] in (16, 32)
+        assert plan["images"] == 1 and plan["tile_h"] in ((16, 32, 64) if method == 0 else (16, 32))
         if plan["tuned"]:
-            assert plan["us_h32"] > 0 and plan["us_h16"] > 0
-            assert plan["us_chosen"] == min(plan["us_h32"], plan["us_h16"])
-            assert plan["tile_h"] == (16 if plan["us_h16"] < plan["us_h32"] else 32)
+            times = {32: plan["us_h32"], 16: plan["us_h16"]}
+            if method == 0:
+                times[64] = plan["us_h64"]  # 64 x 64 tiles are a FOEED candidate only
+            assert all(t > 0 for t in times.values())
+            assert plan["us_chosen"] == min(times.values()) == times[plan["tile_h"]]
         ua2, _ = solve(f, m, lam, sigma, 8, 3)
         again = fg.last_tile_plan()
         assert again["tuned"] == 0 and again["tile_h"] == plan["tile_h"]  # the choice is cached
         assert torch.equal(ua, ua2)
-        for pol, th in (("h32", 32), ("h16", 16)):
+        for pol, th in (("h32", 32), ("h16", 16), ("h64", 64 if method == 0 else 32)):
             fg.set_tile_policy(pol)
             u, _ = solve(f, m, lam, sigma, 8, 3)
             assert fg.last_tile_plan()["tile_h"] == th
