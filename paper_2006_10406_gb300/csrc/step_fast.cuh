@@ -86,6 +86,15 @@ __device__ __forceinline__ float fsi_update_ff(const float up, const float u, co
     return __fadd_rn(sh, __fadd_rn(sl, ql));
 }
 
+// Two-lane FP32 arithmetic (one instruction for two pixels; each lane rounds
+// exactly as the scalar operation does). a - b is fma(b, -1, a): one rounding
+// of the exact difference, the same value as a plain subtraction.
+__device__ __forceinline__ float2 sub2(const float2 a, const float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 pr(const float *v, const int i) { return make_float2(v[i], v[i + 1]); }
+
 // Eight consecutive floats from shared memory (two float4 loads; s is 16-byte aligned).
 __device__ __forceinline__ void ld8(const float *s, float *o)
 {
@@ -103,38 +112,62 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
                                            const float *uc, const float *ud, const float c4, float *dst, const int PL)
 {
     float o0[4], o1[4], o2[4], o3[4];
+    if (!EED) {
+        // FOEED, per pixel (dx, dy: central differences of u_sigma times 2; u_c: centre):
+        //   qq = dy^2 + 1e-18, pp = dx^2, pq = dx dy, s2 = pp + qq, d = pp - qq
+        //   mu1 = 1 / sqrt(1 + s2 c4), mu3 = sqrt(mu1), k1 = (mu1 - 1)/s2^2, k3 = (mu3 - 1)/s2^2
+        //   hxx, hyy, hxy: the Hessian of u
+        //   e1 = g^T H g = 2 pq hxy + pp hxx + qq hyy, e3 = g^T H g_perp = pq (hyy - hxx) + d hxy
+        //   T_xx = hxx + k1 e1 pp - k3 e3 2pq, T_xy = hxy + k1 e1 pq + k3 e3 d,
+        //   T_yy = hyy + k1 e1 qq + k3 e3 2pq
+        // The offset in qq keeps 1/s2^2 finite for a zero gradient (where mu1 = mu3 = 1
+        // and the corrections vanish); it is below the rounding of any dy^2 > 1e-11.
+        // Evaluated in pixel pairs (k, k+1) with two-lane instructions: the operands of
+        // the x differences and of the cross term sit in aligned register pairs of the
+        // float4 loads; the y difference and the centre terms are formed lane by lane.
+        // Each product with a negated factor is an exact sign flip of the scalar one.
+        const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float dx = __fsub_rn(sc[2 + k], sc[k]);
-        const float dy = __fsub_rn(sdn[1 + k], sup[1 + k]);
-        const float ucv = uc[3 + k];
-        if (!EED) {
-            // the offset keeps 1/s2^2 finite for a zero gradient (where mu1 = mu3 = 1
-            // and the corrections vanish); it is below the rounding of any dy^2 > 1e-11
-            const float qq = __fmaf_rn(dy, dy, 1e-18f);
-            const float pp = __fmul_rn(dx, dx);
-            const float pq = __fmul_rn(dx, dy);
-            const float s2 = __fadd_rn(pp, qq);
-            const float mu1 = rsqrt_fast(__fmaf_rn(s2, c4, 1.f));
-            const float inv = rcp_fast(s2);
-            const float inv2 = __fmul_rn(inv, inv);
-            const float k1 = __fmaf_rn(mu1, inv2, -inv2);  // (mu1 - 1) / s2^2
-            const float mu3 = sqrt_fast(mu1);
-            const float k3n = __fmaf_rn(-mu3, inv2, inv2);  // (1 - mu3) / s2^2
-            const float hxx = __fmaf_rn(-2.f, ucv, __fadd_rn(uc[2 + k], uc[4 + k]));
-            const float hyy = __fmaf_rn(-2.f, ucv, __fadd_rn(uu[3 + k], ud[3 + k]));
-            const float hxy =
-                __fmul_rn(__fsub_rn(__fadd_rn(ud[4 + k], uu[2 + k]), __fadd_rn(ud[2 + k], uu[4 + k])), 0.25f);
-            const float d = __fsub_rn(pp, qq);
-            const float pq2 = __fadd_rn(pq, pq);
-            const float e1 = __fmaf_rn(pq2, hxy, __fmaf_rn(pp, hxx, __fmul_rn(qq, hyy)));  // g^T H g
-            const float e3 = __fmaf_rn(pq, __fsub_rn(hyy, hxx), __fmul_rn(d, hxy));         // g^T H g_perp
-            const float a = __fmul_rn(k1, e1);
-            const float bn = __fmul_rn(k3n, e3);
-            o0[k] = __fmaf_rn(a, pp, __fmaf_rn(bn, pq2, hxx));   // T_xx
-            o1[k] = __fmaf_rn(a, pq, __fmaf_rn(-bn, d, hxy));    // T_xy
-            o2[k] = __fmaf_rn(a, qq, __fmaf_rn(-bn, pq2, hyy));  // T_yy
-        } else {
+        for (int k = 0; k < 4; k += 2) {
+            const float2 dx = sub2(pr(sc, 2 + k), pr(sc, k));
+            const float2 dy = make_float2(__fsub_rn(sdn[1 + k], sup[1 + k]), __fsub_rn(sdn[2 + k], sup[2 + k]));
+            const float2 qq = __ffma2_rn(dy, dy, make_float2(1e-18f, 1e-18f));
+            const float2 pp = __fmul2_rn(dx, dx);
+            const float2 pq = __fmul2_rn(dx, dy);
+            const float2 s2 = __fadd2_rn(pp, qq);
+            const float2 t = __ffma2_rn(s2, make_float2(c4, c4), make_float2(1.f, 1.f));
+            const float2 mu1 = make_float2(rsqrt_fast(t.x), rsqrt_fast(t.y));
+            const float2 inv = make_float2(rcp_fast(s2.x), rcp_fast(s2.y));
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 ninv2 = __fmul2_rn(inv2, m1);
+            const float2 k1 = __ffma2_rn(mu1, inv2, ninv2);
+            const float2 mu3 = make_float2(sqrt_fast(mu1.x), sqrt_fast(mu1.y));
+            const float2 k3 = __ffma2_rn(mu3, inv2, ninv2);
+            const float2 sxx = __fadd2_rn(pr(uc, 2 + k), pr(uc, 4 + k));
+            const float2 hxx = make_float2(__fmaf_rn(-2.f, uc[3 + k], sxx.x), __fmaf_rn(-2.f, uc[4 + k], sxx.y));
+            const float2 hyy = make_float2(__fmaf_rn(-2.f, uc[3 + k], __fadd_rn(uu[3 + k], ud[3 + k])),
+                                           __fmaf_rn(-2.f, uc[4 + k], __fadd_rn(uu[4 + k], ud[4 + k])));
+            const float2 hxy = __fmul2_rn(sub2(__fadd2_rn(pr(ud, 4 + k), pr(uu, 2 + k)),
+                                               __fadd2_rn(pr(ud, 2 + k), pr(uu, 4 + k))),
+                                          make_float2(0.25f, 0.25f));
+            const float2 d = sub2(pp, qq);
+            const float2 pq2 = __fadd2_rn(pq, pq);
+            const float2 e1 = __ffma2_rn(pq2, hxy, __ffma2_rn(pp, hxx, __fmul2_rn(qq, hyy)));
+            const float2 e3 = __ffma2_rn(pq, sub2(hyy, hxx), __fmul2_rn(d, hxy));
+            const float2 a = __fmul2_rn(k1, e1);
+            const float2 b = __fmul2_rn(k3, e3);
+            const float2 txx = __ffma2_rn(a, pp, __ffma2_rn(b, __fmul2_rn(pq2, m1), hxx));
+            const float2 txy = __ffma2_rn(a, pq, __ffma2_rn(b, d, hxy));
+            const float2 tyy = __ffma2_rn(a, qq, __ffma2_rn(b, pq2, hyy));
+            o0[k] = txx.x; o0[k + 1] = txx.y;
+            o1[k] = txy.x; o1[k + 1] = txy.y;
+            o2[k] = tyy.x; o2[k + 1] = tyy.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dx = __fsub_rn(sc[2 + k], sc[k]);
+            const float dy = __fsub_rn(sdn[1 + k], sup[1 + k]);
             // A zero gradient gets v1 = (1, 0): the tiny offset leaves every
             // representable non-negligible dx unchanged.
             float dxe = dx + 1e-18f;
@@ -434,13 +467,23 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                 ld8(t0 + 2 * PL + G::ST_W, yc);
                 ld8(t0 + PL - G::ST_W, da);
                 ld8(t0 + PL + G::ST_W, db);
+                // per pixel c (T index 1 + k): Pu = (dxx + dyy) + dxy with
+                //   dxx = (xx[c-1] + xx[c+1]) - 2 xx[c], dyy = (ya[c] + yc[c]) - 2 yb[c],
+                //   dxy = ((db[c+1] + da[c-1]) - (db[c-1] + da[c+1])) / 2,
+                // in pixel pairs: the x neighbours and the cross term in two-lane instructions
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 4; k += 2) {
                     const int c = 1 + k;
-                    float dxx = (xx[c - 1] + xx[c + 1]) - 2.f * xx[c];
-                    float dyy = (ya[c] + yc[c]) - 2.f * yb[c];
-                    float dxy = ((db[c + 1] + da[c - 1]) - (db[c - 1] + da[c + 1])) * 0.5f;
-                    Pu[k] = (dxx + dyy) + dxy;
+                    const float2 sxx = __fadd2_rn(pr(xx, c - 1), pr(xx, c + 1));
+                    const float2 dxx = make_float2(__fmaf_rn(-2.f, xx[c], sxx.x), __fmaf_rn(-2.f, xx[c + 1], sxx.y));
+                    const float2 dyy = make_float2(__fmaf_rn(-2.f, yb[c], __fadd_rn(ya[c], yc[c])),
+                                                   __fmaf_rn(-2.f, yb[c + 1], __fadd_rn(ya[c + 1], yc[c + 1])));
+                    const float2 dxy = __fmul2_rn(sub2(__fadd2_rn(pr(db, c + 1), pr(da, c - 1)),
+                                                       __fadd2_rn(pr(db, c - 1), pr(da, c + 1))),
+                                                  make_float2(0.5f, 0.5f));
+                    const float2 P2 = __fadd2_rn(__fadd2_rn(dxx, dyy), dxy);
+                    Pu[k] = P2.x;
+                    Pu[k + 1] = P2.y;
                 }
             } else {
                 float ac[8], qxr[8], qyu[8], qyd[8], uu[4], ud[4], ucx[8];
@@ -501,18 +544,24 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                 }
             }
             float un[4];
+            if (sizeof(U) == sizeof(double)) {  // the extended-precision update
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if ((pre_mk[e] >> (8 * k)) & 0xffu) {
-                    un[k] = ucv[k];
-                } else if (sizeof(U) == sizeof(double)) {  // the extended-precision update
+                for (int k = 0; k < 4; ++k)
                     un[k] = fsi_update_ff(upv[k], ucv[k], Pu[k], p.alpha_t, p.alpha_lo, p.tau_t, p.tau_lo);
-                } else {
-                    const float up = upv[k];
-                    const float ex = __fmaf_rn(-tau, Pu[k], ucv[k]);  // u^k - tau P u^k
-                    un[k] = __fmaf_rn(alpha, __fsub_rn(ex, up), up);
+            } else {
+                // per pixel: e = u^k - tau P u^k, u^{k+1} = u^{k-1} + alpha (e - u^{k-1}), in pixel pairs
+#pragma unroll
+                for (int k = 0; k < 4; k += 2) {
+                    const float2 up = pr(upv, k);
+                    const float2 ex = __ffma2_rn(make_float2(-tau, -tau), pr(Pu, k), pr(ucv, k));
+                    const float2 nu = __ffma2_rn(make_float2(alpha, alpha), sub2(ex, up), up);
+                    un[k] = nu.x;
+                    un[k + 1] = nu.y;
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((pre_mk[e] >> (8 * k)) & 0xffu) un[k] = ucv[k];  // known pixels keep u^k
             if (p.residual) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
@@ -558,7 +607,7 @@ constexpr long long kFastSmallTiles = 304;
 
 // One FSI step over one image, one CTA per 64 x TH tile.
 template <int R, bool EED, typename U, int TH>
-__global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR) fsi_step_fast(const StepArgs<float> p)
+__global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR, 1024 / FastTile<R, EED, TH>::NTHR) fsi_step_fast(const StepArgs<float> p)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[64];
@@ -580,7 +629,7 @@ __global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR) fsi_step_fast(cons
 // Batched FOEED or EED: one launch per FSI step over the tiles of many images.
 
 template <int R, bool EED, typename U>
-__global__ void __launch_bounds__(256) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
+__global__ void __launch_bounds__(256, 4) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[64];
