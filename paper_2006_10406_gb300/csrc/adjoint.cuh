@@ -355,49 +355,70 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
 // the x pass produces 8 outputs per item, the y pass 2 rows per item, and the
 // tensor stage 4 consecutive positions per item from float4 shared loads.
 
-// The adjoint arithmetic of one position (the same operations as adj_b1_kernel's
-// FP32 branch): T_w = D : W and, when want_q, q = d/d(grad u_sigma) of W : D : H.
-__device__ __forceinline__ void adj_position_f32(const float gx, const float gy, const float hxx, const float hyy,
-                                                 const float hxy, const float wxx, const float wyy, const float wxy,
-                                                 const float inv_l2, const float l2, const bool want_q, float &txx,
-                                                 float &txy, float &tyy, float &qx, float &qy)
+// Two-lane FP32 arithmetic: a - b as fma(b, -1, a) (one rounding, as a subtraction);
+// an aligned register pair of a float array.
+__device__ __forceinline__ float2 adj_sub2(const float2 a, const float2 b)
 {
-    const float rho2 = gx * gx + gy * gy;
-    const float t = fmaf(rho2, inv_l2, 1.f);
-    const float mu1 = adj_rsqrt(t);
-    const float sq = t * mu1;  // 1 / mu1
-    const float mu3 = adj_sqrt(mu1);
-    float C = 1.f, S = 0.f;
-    if (rho2 != 0.f) {
-        const float inv = adj_rcp(rho2);
-        C = (gx * gx - gy * gy) * inv;
-        S = 2.f * gx * gy * inv;
-    }
-    const float Ah = (hxx + hyy) * 0.5f, Bh = (hxx - hyy) * 0.5f;
-    const float Aw = (wxx + wyy) * 0.5f, Bw = (wxx - wyy) * 0.5f;
-    const float h11 = Ah + C * Bh + S * hxy, h22 = Ah - C * Bh - S * hxy, h12 = C * hxy - S * Bh;
-    const float w11 = Aw + C * Bw + S * wxy, w22 = Aw - C * Bw - S * wxy, w12 = C * wxy - S * Bw;
-    const float pp = mu1 * w11, qq = w22, rr = mu3 * w12;
-    const float hs = (pp + qq) * 0.5f, hd = (pp - qq) * 0.5f;
-    txx = hs + C * hd - S * rr;
-    txy = S * hd + C * rr;
-    tyy = hs - C * hd + S * rr;
-    if (want_q) {
-        // sq = 1/mu1 and mu3 = sqrt(mu1), so sqrt(sq) = 1/mu3 = mu3 sq; the two
-        // reciprocals share one: with A = l2 (sq + 1) and B = rs (rs + 1),
-        // 1/(A sq) = B / (A sq B) and 1/(A B) = sq / (A sq B)
-        const float dmu1 = -mu1 * mu1 * mu1 * (0.5f * inv_l2);
-        const float rs = mu3 * sq;
-        const float dmu3 = dmu1 * 0.5f * rs;
-        const float A = l2 * (sq + 1.f), B = rs * (rs + 1.f);
-        const float rAB = adj_rcp(A * sq * B);
-        const float c1 = B * rAB;
-        const float c3 = sq * rAB;
-        const float srho = dmu1 * w11 * h11 + 2.f * dmu3 * w12 * h12;
-        const float th = -c1 * 2.f * (w12 * h11 + w11 * h12) - 2.f * c3 * (-(w11 - w22) * h12 - w12 * (h11 - h22));
-        qx = 2.f * gx * srho - gy * th;
-        qy = 2.f * gy * srho + gx * th;
-    }
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 adj_pr(const float *v, const int i) { return make_float2(v[i], v[i + 1]); }
+
+// The adjoint arithmetic of two positions (the algebra of adj_b1_kernel's FP32
+// branch), in two-lane instructions with the MUFU approximations lane by lane:
+// T_w = D : W and q = d/d(grad u_sigma) of W : D : H, formed for both lanes.
+// In the rotated frame of grad u_sigma (C = cos 2theta, S = sin 2theta), with
+// sq = 1/mu1, mu3 = sqrt(mu1) (so sqrt(sq) = 1/mu3 = mu3 sq = rs):
+//   T_w = (mu1 w11 v1 v1^T + w22 v2 v2^T) + mu3 w12 (v1 v2^T + v2 v1^T)
+//   srho = dmu1 w11 h11 + 2 dmu3 w12 h12, th = 2 (c3 e3 - c1 e1),
+//   e1 = w12 h11 + w11 h12, e3 = (w11 - w22) h12 + w12 (h11 - h22),
+//   q = 2 srho grad u_sigma + th grad u_sigma^perp,
+// where the two reciprocals c1 = 1/(A sq), c3 = 1/(A B) (A = l2 (sq + 1),
+// B = rs (rs + 1)) share one: c1 = B / (A sq B), c3 = sq / (A sq B).
+__device__ __forceinline__ void adj_position_f32x2(const float2 gx, const float2 gy, const float2 hxx,
+                                                   const float2 hyy, const float2 hxy, const float2 wxx,
+                                                   const float2 wyy, const float2 wxy, const float inv_l2,
+                                                   const float l2, float2 &txx, float2 &txy, float2 &tyy,
+                                                   float2 &qx, float2 &qy)
+{
+    const float2 half = make_float2(0.5f, 0.5f), m1 = make_float2(-1.f, -1.f);
+    const float2 gx2 = __fmul2_rn(gx, gx), gy2 = __fmul2_rn(gy, gy);
+    const float2 rho2 = __fadd2_rn(gx2, gy2);
+    const float2 t = __ffma2_rn(rho2, make_float2(inv_l2, inv_l2), make_float2(1.f, 1.f));
+    const float2 mu1 = make_float2(adj_rsqrt(t.x), adj_rsqrt(t.y));
+    const float2 sq = __fmul2_rn(t, mu1);  // 1 / mu1
+    const float2 mu3 = make_float2(adj_sqrt(mu1.x), adj_sqrt(mu1.y));
+    const float2 inv = make_float2(adj_rcp(rho2.x), adj_rcp(rho2.y));
+    float2 C = __fmul2_rn(adj_sub2(gx2, gy2), inv);
+    float2 S = __fmul2_rn(__fmul2_rn(__fadd2_rn(gx, gx), gy), inv);
+    if (rho2.x == 0.f) { C.x = 1.f; S.x = 0.f; }
+    if (rho2.y == 0.f) { C.y = 1.f; S.y = 0.f; }
+    const float2 nC = __fmul2_rn(C, m1), nS = __fmul2_rn(S, m1);
+    const float2 Ah = __fmul2_rn(__fadd2_rn(hxx, hyy), half), Bh = __fmul2_rn(adj_sub2(hxx, hyy), half);
+    const float2 Aw = __fmul2_rn(__fadd2_rn(wxx, wyy), half), Bw = __fmul2_rn(adj_sub2(wxx, wyy), half);
+    const float2 h11 = __ffma2_rn(S, hxy, __ffma2_rn(C, Bh, Ah));
+    const float2 h22 = __ffma2_rn(nS, hxy, __ffma2_rn(nC, Bh, Ah));
+    const float2 h12 = __ffma2_rn(nS, Bh, __fmul2_rn(C, hxy));
+    const float2 w11 = __ffma2_rn(S, wxy, __ffma2_rn(C, Bw, Aw));
+    const float2 w22 = __ffma2_rn(nS, wxy, __ffma2_rn(nC, Bw, Aw));
+    const float2 w12 = __ffma2_rn(nS, Bw, __fmul2_rn(C, wxy));
+    const float2 pp = __fmul2_rn(mu1, w11), rr = __fmul2_rn(mu3, w12);
+    const float2 hs = __fmul2_rn(__fadd2_rn(pp, w22), half), hd = __fmul2_rn(adj_sub2(pp, w22), half);
+    txx = __ffma2_rn(nS, rr, __ffma2_rn(C, hd, hs));
+    txy = __ffma2_rn(S, hd, __fmul2_rn(C, rr));
+    tyy = __ffma2_rn(S, rr, __ffma2_rn(nC, hd, hs));
+    const float2 dmu1 = __fmul2_rn(__fmul2_rn(__fmul2_rn(mu1, mu1), mu1), make_float2(-0.5f * inv_l2, -0.5f * inv_l2));
+    const float2 rs = __fmul2_rn(mu3, sq);
+    const float2 dmu3 = __fmul2_rn(__fmul2_rn(dmu1, half), rs);
+    const float2 A = __ffma2_rn(make_float2(l2, l2), sq, make_float2(l2, l2)), B = __ffma2_rn(rs, rs, rs);
+    const float2 den = __fmul2_rn(__fmul2_rn(A, sq), B);
+    const float2 rAB = make_float2(adj_rcp(den.x), adj_rcp(den.y));
+    const float2 c1 = __fmul2_rn(B, rAB), c3 = __fmul2_rn(sq, rAB);
+    const float2 srho = __ffma2_rn(__fmul2_rn(__fadd2_rn(dmu3, dmu3), w12), h12, __fmul2_rn(__fmul2_rn(dmu1, w11), h11));
+    const float2 e1 = __ffma2_rn(w12, h11, __fmul2_rn(w11, h12));
+    const float2 e3 = __ffma2_rn(adj_sub2(w11, w22), h12, __fmul2_rn(w12, adj_sub2(h11, h22)));
+    const float2 th = __fmul2_rn(adj_sub2(__fmul2_rn(c3, e3), __fmul2_rn(c1, e1)), make_float2(2.f, 2.f));
+    qx = adj_sub2(__fmul2_rn(__fadd2_rn(gx, gx), srho), __fmul2_rn(gy, th));
+    qy = __ffma2_rn(gx, th, __fmul2_rn(__fadd2_rn(gy, gy), srho));
 }
 
 template <int R>
@@ -415,7 +436,7 @@ struct AdjFast {
 };
 
 template <int R>
-__global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
+__global__ void __launch_bounds__(256, 3) adj_b1_fast(const AdjArgs<float> a)
 {
     using G = AdjFast<R>;
     constexpr int TW = G::TW, TH = G::TH, HL = G::HL;
@@ -556,23 +577,41 @@ __global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
             ld_8f(vp, vu); ld_8f(vp + G::VS, vc); ld_8f(vp + 2 * G::VS, vd);
             float o0[4], o1[4], o2[4];
             const int gyp = y0 + r - 1;
+            const float2 half = make_float2(0.5f, 0.5f), quarter = make_float2(0.25f, 0.25f);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float gx = (sc[k + 2] - sc[k]) * 0.5f, gy = (sd[k + 1] - su[k + 1]) * 0.5f;
-                const float hxx = (xc[k + 2] + xc[k + 4]) - 2.f * xc[k + 3];
-                const float hyy = (xu[k + 3] + xd[k + 3]) - 2.f * xc[k + 3];
-                const float hxy = ((xd[k + 4] + xu[k + 2]) - (xd[k + 2] + xu[k + 4])) * 0.25f;
-                const float wxx = (vc[k + 2] + vc[k + 4]) - 2.f * vc[k + 3];
-                const float wyy = (vu[k + 3] + vd[k + 3]) - 2.f * vc[k + 3];
-                const float wxy = ((vd[k + 4] + vu[k + 2]) - (vd[k + 2] + vu[k + 4])) * 0.25f;
-                const int c = 4 * q + k, gxp = x0 + c - 1;
-                const bool want_q = r >= 1 && r <= TH && c >= 1 && c <= TW && gxp < w && gyp < h;
-                float qx = 0.f, qy = 0.f;
-                adj_position_f32(gx, gy, hxx, hyy, hxy, wxx, wyy, wxy, inv_l2, l2, want_q, o0[k], o1[k], o2[k], qx, qy);
-                if (want_q) {
-                    const long gi = (long)gyp * pitch + gxp;
-                    a.qx[gi] = qx;
-                    a.qy[gi] = qy;
+            for (int k = 0; k < 4; k += 2) {
+                // positions k, k+1: x differences and cross terms from aligned pairs, the
+                // y differences and centre terms lane by lane
+                const float2 gx = __fmul2_rn(adj_sub2(adj_pr(sc, k + 2), adj_pr(sc, k)), half);
+                const float2 gy = make_float2((sd[k + 1] - su[k + 1]) * 0.5f, (sd[k + 2] - su[k + 2]) * 0.5f);
+                const float2 sxh = __fadd2_rn(adj_pr(xc, k + 2), adj_pr(xc, k + 4));
+                const float2 hxx = make_float2(fmaf(-2.f, xc[k + 3], sxh.x), fmaf(-2.f, xc[k + 4], sxh.y));
+                const float2 hyy = make_float2(fmaf(-2.f, xc[k + 3], xu[k + 3] + xd[k + 3]),
+                                               fmaf(-2.f, xc[k + 4], xu[k + 4] + xd[k + 4]));
+                const float2 hxy = __fmul2_rn(adj_sub2(__fadd2_rn(adj_pr(xd, k + 4), adj_pr(xu, k + 2)),
+                                                       __fadd2_rn(adj_pr(xd, k + 2), adj_pr(xu, k + 4))),
+                                              quarter);
+                const float2 swv = __fadd2_rn(adj_pr(vc, k + 2), adj_pr(vc, k + 4));
+                const float2 wxx = make_float2(fmaf(-2.f, vc[k + 3], swv.x), fmaf(-2.f, vc[k + 4], swv.y));
+                const float2 wyy = make_float2(fmaf(-2.f, vc[k + 3], vu[k + 3] + vd[k + 3]),
+                                               fmaf(-2.f, vc[k + 4], vu[k + 4] + vd[k + 4]));
+                const float2 wxy = __fmul2_rn(adj_sub2(__fadd2_rn(adj_pr(vd, k + 4), adj_pr(vu, k + 2)),
+                                                       __fadd2_rn(adj_pr(vd, k + 2), adj_pr(vu, k + 4))),
+                                              quarter);
+                float2 t0, t1, t2, qx, qy;
+                adj_position_f32x2(gx, gy, hxx, hyy, hxy, wxx, wyy, wxy, inv_l2, l2, t0, t1, t2, qx, qy);
+                o0[k] = t0.x; o0[k + 1] = t0.y;
+                o1[k] = t1.x; o1[k + 1] = t1.y;
+                o2[k] = t2.x; o2[k + 1] = t2.y;
+                const bool rin = r >= 1 && r <= TH && gyp < h;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int c = 4 * q + k + j, gxp = x0 + c - 1;
+                    if (rin && c >= 1 && c <= TW && gxp < w) {
+                        const long gi = (long)gyp * pitch + gxp;
+                        a.qx[gi] = j ? qx.y : qx.x;
+                        a.qy[gi] = j ? qy.y : qy.x;
+                    }
                 }
             }
             float *dst = tw + r * G::QS + 4 * q;
@@ -594,12 +633,17 @@ __global__ void __launch_bounds__(256, 4) adj_b1_fast(const AdjArgs<float> a)
             ld_8f(t0 + PL - G::QS, du); ld_8f(t0 + PL + G::QS, dd);
             float o[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 4; k += 2) {  // pixel pairs, as in the forward output stage
                 const int c = 1 + k;
-                const float dxx = (xx[c - 1] + xx[c + 1]) - 2.f * xx[c];
-                const float dyy = (yu[c] + yd[c]) - 2.f * yc[c];
-                const float dxy = ((dd[c + 1] + du[c - 1]) - (dd[c - 1] + du[c + 1])) * 0.5f;
-                o[k] = (dxx + dyy) + dxy;
+                const float2 sxx = __fadd2_rn(adj_pr(xx, c - 1), adj_pr(xx, c + 1));
+                const float2 dxx = make_float2(fmaf(-2.f, xx[c], sxx.x), fmaf(-2.f, xx[c + 1], sxx.y));
+                const float2 dyy = make_float2(fmaf(-2.f, yc[c], yu[c] + yd[c]), fmaf(-2.f, yc[c + 1], yu[c + 1] + yd[c + 1]));
+                const float2 dxy = __fmul2_rn(adj_sub2(__fadd2_rn(adj_pr(dd, c + 1), adj_pr(du, c - 1)),
+                                                       __fadd2_rn(adj_pr(dd, c - 1), adj_pr(du, c + 1))),
+                                              make_float2(0.5f, 0.5f));
+                const float2 pv = __fadd2_rn(__fadd2_rn(dxx, dyy), dxy);
+                o[k] = pv.x;
+                o[k + 1] = pv.y;
             }
             const long gi = (long)gyp * pitch + gxp;
             if (gxp + 3 < w) {

@@ -200,6 +200,9 @@ struct FastTile {
     static constexpr int TW = 64, TH = TH_;
     static_assert(TH == 64 || TH == 32 || TH == 16, "tile height");
     static constexpr int NTHR = TH == 64 ? 512 : 256;    // threads per CTA
+    // CTAs per SM the register allocation is bounded for: FOEED's 54 KB of shared
+    // memory fits four 256-thread CTAs (64 registers each), EED's 63 KB three
+    static constexpr int MINB = EED ? 3 : 1024 / NTHR;
     static constexpr int HL = R + 2;
     static constexpr int SU_W = 84, SU_H = TH + 2 * HL;  // u: columns tile-8 .. tile+75
     // Row strides are an odd number of float4 so that the column-major stages
@@ -607,7 +610,7 @@ constexpr long long kFastSmallTiles = 304;
 
 // One FSI step over one image, one CTA per 64 x TH tile.
 template <int R, bool EED, typename U, int TH>
-__global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR, 1024 / FastTile<R, EED, TH>::NTHR) fsi_step_fast(const StepArgs<float> p)
+__global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR, FastTile<R, EED, TH>::MINB) fsi_step_fast(const StepArgs<float> p)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[64];
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(FastTile<R, EED, TH>::NTHR, 1024 / FastTile<R,
 // Batched FOEED or EED: one launch per FSI step over the tiles of many images.
 
 template <int R, bool EED, typename U>
-__global__ void __launch_bounds__(256, 4) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
+__global__ void __launch_bounds__(256, FastTile<R, EED>::MINB) fsi_batch_step_fast(const StepArgs<float> p, const BatchArgs b)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[64];
