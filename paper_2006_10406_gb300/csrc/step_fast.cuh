@@ -10,7 +10,7 @@
 //      the image border)
 //   B  Gaussian x pass, 8 outputs per item, columns tile-2 .. tile+69, every window row
 //   C  Gaussian y pass, 6 rows per item, columns tile-2 .. tile+65
-//   D  gradient, mu1/mu3, Hessian and T (FOEED) or the EED fluxes on tile+-1,
+//   D  gradient, mu1/mu3, Hessian and T (FOEED) or the EED tensor D on tile+-1,
 //      segments of three (or two) rows per item sharing their u_sigma and u rows
 //   E  outer divergence, masked FSI update, optional cycle residual, float4 store;
 //      two rows per thread sharing two T_yy rows
@@ -106,12 +106,12 @@ __device__ __forceinline__ void ld8(const float *s, float *o)
 // One row of four T groups of stage D. sup/sc/sdn: u_sigma rows above/at/below
 // (cols 4q .. 4q+7 of ss: this group's pixels are 1..4), uu/uc/ud: u rows (cols
 // 4q+4 .. 4q+11 of su: pixels 3..6). FOEED writes T_xx, T_xy, T_yy to planes
-// 0..2; EED writes a, c, b d_y u, b d_x u to planes 0..3.
+// 0..2; EED writes the entries a, c, b of D = [[a, b], [b, c]] to planes 0..2.
 template <bool EED>
 __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, const float *sdn, const float *uu,
                                            const float *uc, const float *ud, const float c4, float *dst, const int PL)
 {
-    float o0[4], o1[4], o2[4], o3[4];
+    float o0[4], o1[4], o2[4];
     if (!EED) {
         // FOEED, per pixel (dx, dy: central differences of u_sigma times 2; u_c: centre):
         //   qq = dy^2 + 1e-18, pp = dx^2, pq = dx dy, s2 = pp + qq, d = pp - qq
@@ -183,14 +183,12 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
             float b = S * m1 * 0.5f;
             o0[k] = a;
             o1[k] = cc;
-            o2[k] = b * ((ud[3 + k] - uu[3 + k]) * 0.5f);  // b * d_y u
-            o3[k] = b * ((uc[4 + k] - uc[2 + k]) * 0.5f);  // b * d_x u
+            o2[k] = b;
         }
     }
     *reinterpret_cast<float4 *>(dst) = make_float4(o0[0], o0[1], o0[2], o0[3]);
     *reinterpret_cast<float4 *>(dst + PL) = make_float4(o1[0], o1[1], o1[2], o1[3]);
     *reinterpret_cast<float4 *>(dst + 2 * PL) = make_float4(o2[0], o2[1], o2[2], o2[3]);
-    if (EED) *reinterpret_cast<float4 *>(dst + 3 * PL) = make_float4(o3[0], o3[1], o3[2], o3[3]);
 }
 
 // Tile geometry: 64 x TH output pixels, TH = 32 (large images) or 16 (images
@@ -200,9 +198,9 @@ struct FastTile {
     static constexpr int TW = 64, TH = TH_;
     static_assert(TH == 64 || TH == 32 || TH == 16, "tile height");
     static constexpr int NTHR = TH == 64 ? 512 : 256;    // threads per CTA
-    // CTAs per SM the register allocation is bounded for: FOEED's 54 KB of shared
-    // memory fits four 256-thread CTAs (64 registers each), EED's 63 KB three
-    static constexpr int MINB = EED ? 3 : 1024 / NTHR;
+    // CTAs per SM the register allocation is bounded for: the 54 KB of shared
+    // memory of a 64 x 32 tile fit four 256-thread CTAs (64 registers each)
+    static constexpr int MINB = 1024 / NTHR;
     static constexpr int HL = R + 2;
     static constexpr int SU_W = 84, SU_H = TH + 2 * HL;  // u: columns tile-8 .. tile+75
     // Row strides are an odd number of float4 so that the column-major stages
@@ -210,7 +208,7 @@ struct FastTile {
     static constexpr int SX_W = 76, SX_H = SU_H;         // x pass: columns tile-2 .. tile+69 (+4 pad)
     static constexpr int SS_W = 76, SS_H = TH + 4;       // u_sigma: rows tile-2 .. tile+33
     static constexpr int ST_W = 68, ST_H = TH + 2;       // T: rows/cols tile-1 .. (cols to tile+66)
-    static constexpr int NT = EED ? 4 : 3;
+    static constexpr int NT = 3;  // T planes
     // the T planes reuse the x-pass buffer, which is dead after stage C
     static constexpr int SXT = (SX_W * SX_H > NT * ST_W * ST_H) ? SX_W * SX_H : NT * ST_W * ST_H;
     static constexpr int ELEMS = SU_W * SU_H + SXT + SS_W * SS_H;
@@ -440,8 +438,9 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
         // FOEED: T_xx row, T_yy rows r .. r+2 and T_xy rows r, r+2 (T rows) of output row r-1;
         // the second output row reuses two of the T_yy rows
         float xx[8], ya[8], yb[8], yc[8], da[8], db[8];
-        // EED: plane-1 rows r .. r+2 (the second output row reuses two) and the u rows
-        float cu[8], cc[8], cd[8], ud4[4], uc4[4];
+        // EED: plane-1 rows r .. r+2 (the second output row reuses two); the row below's
+        // u values, which are the second output row's own
+        float cu[8], cc[8], cd[8], ud4[4];
 #pragma unroll
         for (int e = 0; e < ER; ++e) {
             const int r = re + e;
@@ -489,7 +488,12 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                     Pu[k + 1] = P2.y;
                 }
             } else {
-                float ac[8], qxr[8], qyu[8], qyd[8], uu[4], ud[4], ucx[8];
+                // a (plane 0) on this row, c (plane 1) and b (plane 2) on T rows r .. r+2;
+                // u rows tile row-1 .. row+1 at su cols 4q+4 .. 4q+12 (xa/xc/xb[j] <-> col 4q+4+j,
+                // pixel k at j = 4 + k). The products b d_y u (differentiated in x) and b d_x u
+                // (in y) are formed here at the neighbour positions, as rounded products of
+                // the same operands in the same order as a stored plane of them would hold.
+                float ac[8], bm[8], bu[8], bd[8], xa[9], xc[9], xb[9];
                 ld8(t0, ac);
                 if (e == 0) {
                     ld8(t0 + PL - G::ST_W, cu);
@@ -499,37 +503,31 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
                     for (int k = 0; k < 8; ++k) { cu[k] = cc[k]; cc[k] = cd[k]; }
                 }
                 ld8(t0 + PL + G::ST_W, cd);
-                ld8(t0 + 2 * PL, qxr);
-                ld8(t0 + 3 * PL - G::ST_W, qyu);
-                ld8(t0 + 3 * PL + G::ST_W, qyd);
-                // u neighbours: su cols 4q+7 .. 4q+12 <-> ucx[3..8]; load su cols 4q+4 .. 4q+11 and 4q+12
-                ld8(um - 4, ucx);
-                float ur = um[4];
-                if (e == 0) {
-                    const float4 a = *reinterpret_cast<const float4 *>(um - G::SU_W);
-                    uu[0] = a.x; uu[1] = a.y; uu[2] = a.z; uu[3] = a.w;
-                } else {  // the row above is the first output row's own
+                ld8(t0 + 2 * PL, bm);
+                ld8(t0 + 2 * PL - G::ST_W, bu);
+                ld8(t0 + 2 * PL + G::ST_W, bd);
+                ld8(um - 4 - G::SU_W, xa);
+                xa[8] = um[4 - G::SU_W];
+                ld8(um - 4, xc);
+                xc[8] = um[4];
+                ld8(um - 4 + G::SU_W, xb);
+                xb[8] = um[4 + G::SU_W];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) uu[k] = uc4[k];
-                }
-                {
-                    const float4 a = *reinterpret_cast<const float4 *>(um + G::SU_W);
-                    ud[0] = a.x; ud[1] = a.y; ud[2] = a.z; ud[3] = a.w;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { uc4[k] = ucv[k]; ud4[k] = ud[k]; }
+                for (int k = 0; k < 4; ++k) ud4[k] = xb[4 + k];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int c = 1 + k;
-                    float u0 = ucv[k];
-                    float ul = ucx[3 + k];
-                    float urr = (k == 3) ? ur : ucx[5 + k];
+                    const int c = 1 + k, j = 4 + k;
+                    const float u0 = ucv[k];
                     // the fluxes as explicit fma(a, b, -round(c d)): the same bits in every instantiation
-                    float fx = fmaf(ac[c] + ac[c + 1], urr - u0, -__fmul_rn(ac[c - 1] + ac[c], u0 - ul)) * 0.5f;
-                    float fy = fmaf(cc[c] + cd[c], ud[k] - u0, -__fmul_rn(cu[c] + cc[c], u0 - uu[k])) * 0.5f;
-                    // plane 2 holds b * d_y u (differentiated in x), plane 3 b * d_x u (in y)
-                    float mx = qxr[c + 1] - qxr[c - 1];
-                    float my = qyd[c] - qyu[c];
+                    float fx = fmaf(ac[c] + ac[c + 1], xc[j + 1] - u0, -__fmul_rn(ac[c - 1] + ac[c], u0 - xc[j - 1])) * 0.5f;
+                    float fy = fmaf(cc[c] + cd[c], xb[j] - u0, -__fmul_rn(cu[c] + cc[c], u0 - xa[j])) * 0.5f;
+                    // b d_y u at (row, col +- 1), b d_x u at (row +- 1, col)
+                    const float pr_ = __fmul_rn(bm[c + 1], __fmul_rn(__fsub_rn(xb[j + 1], xa[j + 1]), 0.5f));
+                    const float pl_ = __fmul_rn(bm[c - 1], __fmul_rn(__fsub_rn(xb[j - 1], xa[j - 1]), 0.5f));
+                    const float pd_ = __fmul_rn(bd[c], __fmul_rn(__fsub_rn(xb[j + 1], xb[j - 1]), 0.5f));
+                    const float pu_ = __fmul_rn(bu[c], __fmul_rn(__fsub_rn(xa[j + 1], xa[j - 1]), 0.5f));
+                    float mx = __fsub_rn(pr_, pl_);
+                    float my = __fsub_rn(pd_, pu_);
                     Pu[k] = -((fx + fy) + (mx + my) * 0.5f);
                 }
             }
@@ -707,8 +705,8 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
     }
     const int ntx = (ap->w + 63) / 64;
     if constexpr (!EED) {
-        // 64 x 64 tiles, 512 threads, two CTAs per SM (FOEED only: EED's four T
-        // planes would not fit twice in an SM's shared memory)
+        // 64 x 64 tiles, 512 threads, two CTAs per SM (FOEED only: a candidate of
+        // the autotuner that measured slower at every size, not instantiated for EED)
         if (ap->tile_h == 64) {
             using G64 = FastTile<R, EED, 64>;
             dim3 grid(ntx, (ap->h + 63) / 64);
