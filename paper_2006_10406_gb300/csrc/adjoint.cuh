@@ -656,6 +656,175 @@ __global__ void __launch_bounds__(256, 3) adj_b1_fast(const AdjArgs<float> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// B2 for FP32, register-blocked like B1: 64 x 16 tiles, 256 threads.
+//   windows  q_x, q_y rows tile-R-1 .. tile+TH+R, columns tile-12 .. tile+75 (interior
+//            tiles, 16-byte cp.async with one fixed float4 column per thread)
+//   D        -D_odd q on rows tile-R .. tile+TH+R-1, four columns per item from float4
+//            loads (border tiles: per position, with the odd ghosts); column d <-> tile-8+d
+//   x pass   Gaussian along rows of D, 8 outputs per item from six float4 loads
+//   y pass   z = Gaussian along columns, four pixels per thread, then the step's
+//            adjoint recursion with float4 global loads and stores
+// The x-pass output aliases the q windows, which are dead once D is formed.
+template <int R>
+struct AdjB2Fast {
+    static constexpr int TW = 64, TH = kAdjTH;
+    static constexpr int QR = TH + 2 * R + 2, QC = 88;  // q windows
+    static constexpr int DH = TH + 2 * R, DS = 84;       // D: 80 columns used, 21 float4 per row
+    static constexpr int XS = 68;                        // x pass: 64 columns, 17 float4 per row
+    static_assert(DH * XS <= 2 * QR * QC, "x pass fits in the q windows");
+    static constexpr int ELEMS = 2 * QR * QC + DH * DS;
+    static constexpr size_t SMEM = sizeof(float) * ELEMS;
+};
+
+template <int R>
+__global__ void __launch_bounds__(256) adj_b2_fast(const AdjArgs<float> a)
+{
+    using G = AdjB2Fast<R>;
+    constexpr int TW = G::TW, TH = G::TH;
+    extern __shared__ __align__(16) float sm[];
+    float *sqx = sm, *sqy = sm + G::QR * G::QC;  // q windows
+    float *sd = sm + 2 * G::QR * G::QC;           // -D_odd q
+    float *sx = sm;                               // x pass (after D)
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int w = a.w, h = a.h;
+    const long pitch = a.pitch;
+    // D columns 8-R .. 71+R (tile-R .. tile+63+R) are the ones the x pass reads
+    constexpr int M0 = (8 - R) / 4, M1 = (71 + R) / 4, NM = M1 - M0 + 1;
+    const bool inner = x0 - 12 >= 0 && x0 + 76 <= w && y0 - R - 1 >= 0 && y0 + TH + R + 1 <= h;
+    if (inner) {
+        if (tid < 242) {  // 22 float4 columns, 11 rows per pass
+            const int q = tid % 22, r0 = tid / 22;
+            const long go = (long)(y0 - R - 1 + r0) * pitch + (x0 - 12 + 4 * q);
+            uint32_t dx = adj_smem(sqx + r0 * G::QC + 4 * q), dy = adj_smem(sqy + r0 * G::QC + 4 * q);
+            for (int r = r0; r < G::QR; r += 11, dx += 4u * 11 * G::QC, dy += 4u * 11 * G::QC) {
+                const long o = go + (long)(r - r0) * pitch;
+                adj_cp16(dx, a.qx + o);
+                adj_cp16(dy, a.qy + o);
+            }
+        }
+        adj_cp_wait();
+        __syncthreads();
+        // D column d <-> q window column d+4; position group m: D columns 4m .. 4m+3
+        for (int i = tid; i < G::DH * NM; i += 256) {
+            const int r = i / NM, m = M0 + (i - r * NM);
+            const float *px = sqx + (r + 1) * G::QC + 4 * m;  // q_x columns 4m .. 4m+8 <-> x[0..8]
+            float x[9];
+            {
+                const float4 f0 = *reinterpret_cast<const float4 *>(px);
+                const float4 f1 = *reinterpret_cast<const float4 *>(px + 4);
+                x[0] = f0.x; x[1] = f0.y; x[2] = f0.z; x[3] = f0.w; x[4] = f1.x; x[5] = f1.y; x[6] = f1.z; x[7] = f1.w;
+                x[8] = px[8];
+            }
+            const float4 yu = *reinterpret_cast<const float4 *>(sqy + r * G::QC + 4 * m + 4);
+            const float4 yd = *reinterpret_cast<const float4 *>(sqy + (r + 2) * G::QC + 4 * m + 4);
+            float4 o;
+            o.x = -((x[5] - x[3]) + (yd.x - yu.x)) * 0.5f;
+            o.y = -((x[6] - x[4]) + (yd.y - yu.y)) * 0.5f;
+            o.z = -((x[7] - x[5]) + (yd.z - yu.z)) * 0.5f;
+            o.w = -((x[8] - x[6]) + (yd.w - yu.w)) * 0.5f;
+            *reinterpret_cast<float4 *>(sd + r * G::DS + 4 * m) = o;
+        }
+    } else {
+        constexpr int DW = TW + 2 * R;
+        for (int i = tid; i < G::DH * DW; i += 256) {
+            const int r = i / DW, c = i - r * DW;  // tile column c - R
+            sd[r * G::DS + c + 8 - R] = adj_divq(a, mirror_idx(x0 - R + c, w), mirror_idx(y0 - R + r, h));
+        }
+    }
+    __syncthreads();
+    float wt[2 * R + 1];
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) wt[t] = a.wts[t];
+    // x pass: sx row r, column c (tile column c) <- D columns c+8-R .. c+8+R
+    for (int i = tid; i < G::DH * 8; i += 256) {
+        const int r = i >> 3, g = i & 7;
+        const float *src = sd + r * G::DS + 8 * g;
+        float v[24];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float4 f = *reinterpret_cast<const float4 *>(src + 4 * j);
+            v[4 * j] = f.x; v[4 * j + 1] = f.y; v[4 * j + 2] = f.z; v[4 * j + 3] = f.w;
+        }
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t <= 2 * R; ++t) acc = fmaf(wt[t], v[k + 8 - R + t], acc);
+            o[k] = acc;
+        }
+        float *dst = sx + r * G::XS + 8 * g;
+        *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    __syncthreads();
+    // y pass and the recursion: row ty, pixels 4qe .. 4qe+3
+    {
+        const int qe = tid & 15, ty = tid >> 4;
+        const int gy = y0 + ty, gx = x0 + 4 * qe;
+        if (gy < h && gx < w) {
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t <= 2 * R; ++t) {
+                const float4 f = *reinterpret_cast<const float4 *>(sx + (ty + t) * G::XS + 4 * qe);
+                z[0] = fmaf(wt[t], f.x, z[0]);
+                z[1] = fmaf(wt[t], f.y, z[1]);
+                z[2] = fmaf(wt[t], f.z, z[2]);
+                z[3] = fmaf(wt[t], f.w, z[3]);
+            }
+            const long gi = (long)gy * pitch + gx;
+            const bool full = gx + 3 < w;
+            float gv[4], pv[4], pe[4];
+            uint32_t mk = 0;
+            if (full) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(a.g + gi);
+                const float4 p4 = *reinterpret_cast<const float4 *>(a.pv + gi);
+                const float4 e4 = *reinterpret_cast<const float4 *>(a.pend + gi);
+                mk = *reinterpret_cast<const uint32_t *>(a.mask + gi);
+                gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+                pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+                pe[0] = e4.x; pe[1] = e4.y; pe[2] = e4.z; pe[3] = e4.w;
+            } else {
+                for (int k = 0; k < 4; ++k) {
+                    const bool in = gx + k < w;
+                    gv[k] = in ? a.g[gi + k] : 0.f;
+                    pv[k] = in ? a.pv[gi + k] : 0.f;
+                    pe[k] = in ? a.pend[gi + k] : 0.f;
+                    if (in && a.mask[gi + k]) mk |= 0xffu << (8 * k);
+                }
+            }
+            float go[4], pn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool known = ((mk >> (8 * k)) & 0xffu) != 0;
+                const float v = known ? 0.f : gv[k];
+                const float jt = pv[k] + z[k];  // J_F(x)^T v
+                const float dcur = (known ? gv[k] : 0.f) + a.alpha * v - a.alpha * a.tau * jt;
+                const float dprev = (1.f - a.alpha) * v;
+                if (a.first_of_cycle) {
+                    go[k] = pe[k] + dcur + dprev;
+                    pn[k] = 0.f;
+                } else {
+                    go[k] = pe[k] + dcur;
+                    pn[k] = dprev;
+                }
+            }
+            if (full) {
+                *reinterpret_cast<float4 *>(a.gout + gi) = make_float4(go[0], go[1], go[2], go[3]);
+                *reinterpret_cast<float4 *>(a.pend + gi) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (gx + k < w) {
+                        a.gout[gi + k] = go[k];
+                        a.pend[gi + k] = pn[k];
+                    }
+            }
+        }
+    }
+}
+
 template <typename T, int R>
 struct AdjSmem {
     static constexpr int HL = R + 2, TW = adj_tile_w<T>(), TH = kAdjTH;
@@ -677,6 +846,8 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(adj_b1_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjFast<R>::SMEM);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(adj_b2_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjB2Fast<R>::SMEM);
+        if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(adj_b2_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
     }
     dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
@@ -686,7 +857,10 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
         adj_b1_kernel<T, R, TW><<<grid, 256, SM::B1, s>>>(*ap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_b2_kernel<T, R, TW><<<grid, 256, SM::B2, s>>>(*ap);
+    if (sizeof(T) == sizeof(float))
+        adj_b2_fast<R><<<grid, 256, AdjB2Fast<R>::SMEM, s>>>(*reinterpret_cast<const AdjArgs<float> *>(ap));
+    else
+        adj_b2_kernel<T, R, TW><<<grid, 256, SM::B2, s>>>(*ap);
     return cudaGetLastError();
 }
 
