@@ -66,6 +66,23 @@ def test_vjp_f32_matches_oracle(sigma):
     assert np.max(np.abs(gf.cpu().numpy().astype(np.float64) - ref)) <= 2e-3 * scale
 
 
+@pytest.mark.parametrize("h,w", [(96, 224), (97, 226)])
+@pytest.mark.parametrize("sigma", [1.0, 1.5])
+def test_vjp_f32_interior_tiles_match_oracle(h, w, sigma):
+    # wide enough that the FP32 backward kernels' interior tiles (windows copied
+    # whole, without mirroring) occur beside border tiles; 97 x 226 adds a ragged
+    # last row of tiles and a partial last group of four pixels
+    img, mask, gu = _case(h, w, seed=h + w)
+    f32 = img.astype(np.float32)
+    ref, _ = O.inpaint_vjp(f32.astype(np.float64), mask, gu, sigma, 0.03, 8, 3)
+    gf, _ = fg.foeed_inpaint_vjp(torch.from_numpy(f32).to(DEV), torch.from_numpy(mask).to(DEV),
+                                 torch.from_numpy(gu.astype(np.float32)).to(DEV), 0.03, sigma, 8, 3)
+    g = gf.cpu().numpy().astype(np.float64)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(g - ref)) <= 2e-3 * scale
+    assert np.all(g[mask == 0] == 0.0)
+
+
 def test_checkpoint_interval_does_not_change_the_gradient():
     img, mask, gu = _case(40, 44, seed=6)
     args = (torch.from_numpy(img.astype(np.float32)).to(DEV), torch.from_numpy(mask).to(DEV),
