@@ -355,7 +355,19 @@ def adjoint_leg(fg, synth, torch, dev, stream):
         b.record(stream)
         torch.cuda.synchronize(dev)
         grad_ms[f"checkpoint_every_{k}"] = a.elapsed_time(b)
+    # the plain single-image FP32 solve of the same workload (same steps), for comparison
+    solve_ms = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fg.foeed_inpaint(target, md, p["lam"], p["sigma"], n, cycles, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        solve_ms.append(a.elapsed_time(b))
+    plain = min(solve_ms)
     return {"iterations": 20, "mse_start": mse[0], "mse_end": mse[-1], "gradient_ms": grad_ms,
+            "plain_solve_ms": plain,
+            "gradient_over_plain_solve": {k: v / plain for k, v in grad_ms.items()},
             "mse_drop_pct": 100.0 * (mse[0] - mse[-1]) / mse[0],
             "psnr_start_db": float(10 * np.log10(1.0 / mse[0])), "psnr_end_db": float(10 * np.log10(1.0 / mse[-1])),
             "ms_per_iteration": float(np.median(ev)), "unrolled_steps": steps, "checkpoint_every": 16,
@@ -388,7 +400,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-convergence", action="store_true")
-    ap.add_argument("--tile-policy", default="auto", choices=["auto", "h32", "h16"],
+    ap.add_argument("--tile-policy", default="auto", choices=["auto", "h32", "h16", "h64"],
                     help="tile shape of the FP32 step kernel: timed once and kept (auto), or fixed; a fixed "
                          "shape keeps profiler runs, whose serialised launches distort the timing, on the "
                          "shape the benchmark uses")
