@@ -89,7 +89,8 @@ __device__ __forceinline__ void ld_8f(const float *s, float *o)
     const float4 b = *reinterpret_cast<const float4 *>(s + 4);
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
-// B1: P(x) v and q at every pixel of a TW x 16 tile.
+// B1 in FP64 (the FP32 path is adj_b1_fast below): P(x) v and q at every pixel
+// of a TW x 16 tile.
 template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
 {
@@ -181,22 +182,12 @@ __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
         const T *s0 = ss + (r + 1) * SW + (c + 1);
         const T gx = (s0[1] - s0[-1]) * T(0.5), gy = (s0[SW] - s0[-SW]) * T(0.5);
         const T rho2 = gx * gx + gy * gy;
-        T sq, mu1, mu3, C, S;  // sq = 1 / mu1
-        if (sizeof(T) == sizeof(float)) {
-            const float t = fmaf(float(rho2), float(a.inv_l2), 1.f);
-            mu1 = adj_rsqrt(t);
-            sq = t * float(mu1);
-            mu3 = adj_sqrt(float(mu1));
-            const float inv = adj_rcp(float(rho2));
-            if (rho2 == T(0)) { C = T(1); S = T(0); }
-            else { C = (gx * gx - gy * gy) * inv; S = T(2) * gx * gy * inv; }
-        } else {
-            sq = sqrt(T(1) + rho2 / l2);
-            mu1 = T(1) / sq;
-            mu3 = sqrt(mu1);
-            if (rho2 == T(0)) { C = T(1); S = T(0); }
-            else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
-        }
+        T C, S;
+        const T sq = sqrt(T(1) + rho2 / l2);  // 1 / mu1
+        const T mu1 = T(1) / sq;
+        const T mu3 = sqrt(mu1);
+        if (rho2 == T(0)) { C = T(1); S = T(0); }
+        else { C = (gx * gx - gy * gy) / rho2; S = T(2) * gx * gy / rho2; }
         const T *x0p = sxw + (r + 1 + R) * XW + (c + 1 + R + XOFF);
         const T *v0 = sv + (r + 1) * VW + (c + 1 + VOFF);
         const T hxx = (x0p[-1] + x0p[1]) - T(2) * x0p[0];
@@ -222,20 +213,12 @@ __global__ void __launch_bounds__(256) adj_b1_kernel(const AdjArgs<T> a)
         if (r >= 1 && r <= TH && c >= 1 && c <= TW) {
             const int gxp = x0 + c - 1, gyp = y0 + r - 1;
             if (gxp < w && gyp < h) {
-                T dmu1, dmu3, c1, c3;  // d mu1 / d rho^2, d mu3 / d rho^2, (1 - mu1) / rho^2, (1 - mu3) / rho^2
-                if (sizeof(T) == sizeof(float)) {
-                    dmu1 = -mu1 * mu1 * mu1 * (T(0.5) * a.inv_l2);
-                    dmu3 = dmu1 * T(0.5) * adj_rsqrt(float(mu1));
-                    const float rs = adj_sqrt(float(sq));
-                    c1 = adj_rcp(float(l2 * sq * (sq + T(1))));
-                    c3 = adj_rcp(float(l2 * (sq + T(1)) * rs * (rs + T(1))));
-                } else {
-                    dmu1 = -mu1 * mu1 * mu1 / (T(2) * l2);
-                    dmu3 = dmu1 / (T(2) * mu3);
-                    const T rs = sqrt(sq);
-                    c1 = T(1) / (l2 * sq * (sq + T(1)));
-                    c3 = T(1) / (l2 * (sq + T(1)) * rs * (rs + T(1)));
-                }
+                // d mu1 / d rho^2, d mu3 / d rho^2, (1 - mu1) / rho^2, (1 - mu3) / rho^2
+                const T dmu1 = -mu1 * mu1 * mu1 / (T(2) * l2);
+                const T dmu3 = dmu1 / (T(2) * mu3);
+                const T rs = sqrt(sq);
+                const T c1 = T(1) / (l2 * sq * (sq + T(1)));
+                const T c3 = T(1) / (l2 * (sq + T(1)) * rs * (rs + T(1)));
                 const T srho = dmu1 * w11 * h11 + T(2) * dmu3 * w12 * h12;  // d s / d rho^2
                 const T th = -c1 * T(2) * (w12 * h11 + w11 * h12) - T(2) * c3 * (-(w11 - w22) * h12 - w12 * (h11 - h22));
                 const long gi = (long)gyp * pitch + gxp;
@@ -271,7 +254,8 @@ __device__ __forceinline__ T adj_divq(const AdjArgs<T> &a, int x, int y)
     return -((xr - xl) + (yd - yu)) * T(0.5);
 }
 
-// B2: z = G (-D_odd q), then the step's adjoint recursion at every pixel of a tile.
+// B2 in FP64 (the FP32 path is adj_b2_fast below): z = G (-D_odd q), then the
+// step's adjoint recursion at every pixel of a tile.
 template <typename T, int R, int TW>
 __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
 {
@@ -282,36 +266,9 @@ __global__ void __launch_bounds__(256) adj_b2_kernel(const AdjArgs<T> a)
     T *sxp = sr + RW * RH;                    // x pass: RH rows x TW columns
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    // FP32 tiles whose q windows (rows tile-R-1 .. tile+TH+R, columns tile-8 ..
-    // tile+71) lie inside the image copy them to shared memory (16-byte cp.async,
-    // one fixed float4 column per thread) and take -D_odd q from there; the others
-    // read q through L1 with the odd ghosts at the border.
-    constexpr int QR = RH + 2, QC = 80;
-    const bool inner = sizeof(T) == sizeof(float) && x0 - 8 >= 0 && x0 + 72 <= a.w && y0 - R - 1 >= 0 &&
-                       y0 + TH + R + 1 <= a.h;
-    if (inner) {
-        float *sqx = reinterpret_cast<float *>(sxp + RH * TW), *sqy = sqx + QR * QC;
-        if (tid < 240) {
-            const int q = tid % 20, r0 = tid / 20;
-            for (int r = r0; r < QR; r += 12) {
-                const long go = (long)(y0 - R - 1 + r) * a.pitch + (x0 - 8 + 4 * q);
-                adj_cp16(adj_smem(sqx + r * QC + 4 * q), reinterpret_cast<const float *>(a.qx) + go);
-                adj_cp16(adj_smem(sqy + r * QC + 4 * q), reinterpret_cast<const float *>(a.qy) + go);
-            }
-        }
-        adj_cp_wait();
-        __syncthreads();
-        for (int i = tid; i < RW * RH; i += 256) {
-            // position (r, c) <-> pixel (y0-R+r, x0-R+c) <-> window row r+1, column c+8-R
-            const int r = i / RW, c = i - r * RW;
-            const float *px = sqx + (r + 1) * QC + (c + 8 - R), *py = sqy + (r + 1) * QC + (c + 8 - R);
-            sr[i] = T(-((px[1] - px[-1]) + (py[QC] - py[-QC])) * 0.5f);
-        }
-    } else {
-        for (int i = tid; i < RW * RH; i += 256) {
-            int r = i / RW, c = i - r * RW;
-            sr[i] = adj_divq(a, mirror_idx(x0 - R + c, a.w), mirror_idx(y0 - R + r, a.h));
-        }
+    for (int i = tid; i < RW * RH; i += 256) {
+        int r = i / RW, c = i - r * RW;
+        sr[i] = adj_divq(a, mirror_idx(x0 - R + c, a.w), mirror_idx(y0 - R + r, a.h));
     }
     __syncthreads();
     for (int i = tid; i < RH * TW; i += 256) {
@@ -363,8 +320,8 @@ __device__ __forceinline__ float2 adj_sub2(const float2 a, const float2 b)
 }
 __device__ __forceinline__ float2 adj_pr(const float *v, const int i) { return make_float2(v[i], v[i + 1]); }
 
-// The adjoint arithmetic of two positions (the algebra of adj_b1_kernel's FP32
-// branch), in two-lane instructions with the MUFU approximations lane by lane:
+// The adjoint arithmetic of two positions (the algebra of adj_b1_kernel), in
+// two-lane FP32 instructions with the MUFU approximations lane by lane:
 // T_w = D : W and q = d/d(grad u_sigma) of W : D : H, formed for both lanes.
 // In the rotated frame of grad u_sigma (C = cos 2theta, S = sin 2theta), with
 // sq = 1/mu1, mu3 = sqrt(mu1) (so sqrt(sq) = 1/mu3 = mu3 sq = rs):
@@ -831,8 +788,7 @@ struct AdjSmem {
     static constexpr size_t B1 = sizeof(T) * ((TW + 16) * (TH + 2 * HL) + (TW + 8) * (TH + 4) +
                                               (TH + 2 * HL) * (TW + 4) + (TW + 4) * (TH + 4) + 3 * (TW + 2) * (TH + 2)) +
                                  (size_t)(TW + 8) * (TH + 4);
-    static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW) +
-                                 (sizeof(T) == sizeof(float) ? sizeof(float) * 2 * (TH + 2 * R + 2) * 80 : 0);
+    static constexpr size_t B2 = sizeof(T) * ((TW + 2 * R) * (TH + 2 * R) + (TH + 2 * R) * TW);
 };
 
 template <typename T, int R>
@@ -840,28 +796,35 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> *ap, cudaStream_t s)
 {
     using SM = AdjSmem<T, R>;
     constexpr int TW = SM::TW, TH = SM::TH;
-    if (!ap) {
-        cudaError_t e =
-            cudaFuncSetAttribute(adj_b1_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
+    if constexpr (sizeof(T) == sizeof(float)) {  // the register-blocked FP32 kernels
+        if (!ap) {
+            cudaError_t e =
+                cudaFuncSetAttribute(adj_b1_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjFast<R>::SMEM);
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(adj_b2_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)AdjB2Fast<R>::SMEM);
+        }
+        dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
+        adj_b1_fast<R><<<grid, 256, AdjFast<R>::SMEM, s>>>(*ap);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(adj_b1_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjFast<R>::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(adj_b2_fast<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjB2Fast<R>::SMEM);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(adj_b2_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B2);
-    }
-    dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
-    if (sizeof(T) == sizeof(float))
-        adj_b1_fast<R><<<grid, 256, AdjFast<R>::SMEM, s>>>(*reinterpret_cast<const AdjArgs<float> *>(ap));
-    else
+        adj_b2_fast<R><<<grid, 256, AdjB2Fast<R>::SMEM, s>>>(*ap);
+        return cudaGetLastError();
+    } else {
+        if (!ap) {
+            cudaError_t e =
+                cudaFuncSetAttribute(adj_b1_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B1);
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(adj_b2_kernel<T, R, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SM::B2);
+        }
+        dim3 grid((ap->w + TW - 1) / TW, (ap->h + TH - 1) / TH);
         adj_b1_kernel<T, R, TW><<<grid, 256, SM::B1, s>>>(*ap);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (sizeof(T) == sizeof(float))
-        adj_b2_fast<R><<<grid, 256, AdjB2Fast<R>::SMEM, s>>>(*reinterpret_cast<const AdjArgs<float> *>(ap));
-    else
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         adj_b2_kernel<T, R, TW><<<grid, 256, SM::B2, s>>>(*ap);
-    return cudaGetLastError();
+        return cudaGetLastError();
+    }
 }
 
 }  // namespace foeed
