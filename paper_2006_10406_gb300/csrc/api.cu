@@ -330,6 +330,10 @@ cudaError_t capture_stream(int dev, cudaStream_t *out)
 thread_local int g_tile_policy = FOEED_TILES_AUTO;
 thread_local foeed_tile_plan g_last_plan = {};
 
+// The tile height a fixed policy gives one image: 64 x 64 tiles exist for FOEED
+// only, so EED takes 64 x 32 under FOEED_TILES_H64.
+int fixed_tile_h(bool eed) { return (eed && g_tile_policy == FOEED_TILES_H64) ? FOEED_TILES_H32 : g_tile_policy; }
+
 struct TuneKey {
     int dev, eed, R, f64u, w, h, count, pad;
     unsigned long long sizes;  // FNV-1a hash of a batch's image sizes (0 for one image)
@@ -393,7 +397,7 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
     *tile_h = 0;
     if (d == FOEED_F64 || !fast_params(eed, p)) return FOEED_OK;
     if (g_tile_policy != FOEED_TILES_AUTO) {
-        *tile_h = (eed && g_tile_policy == FOEED_TILES_H64) ? 32 : g_tile_policy;
+        *tile_h = fixed_tile_h(eed);
     } else {
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -676,7 +680,7 @@ foeed_status step(bool eed, const void *u_prev, const void *u_cur, void *u_next,
     c.w = w; c.h = h; c.pitch = pitch; c.alpha = alpha;
     c.tau = default_tau(eed, params->tau);
     c.c0 = nullptr; c.ctl = nullptr; c.partials = nullptr; c.residual = 0; c.check_done = 0;
-    c.tile_h = g_tile_policy;
+    c.tile_h = fixed_tile_h(eed);
     CK(launch_step(eed, d, nullptr, *params, static_cast<cudaStream_t>(stream)));
     CK(launch_step(eed, d, &c, *params, static_cast<cudaStream_t>(stream)));
     return FOEED_OK;

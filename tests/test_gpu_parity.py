@@ -454,6 +454,37 @@ def test_fast_step_each_tile_shape_matches_oracle(policy, shape):
     np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
 
 
+@pytest.mark.parametrize("shape", [(100, 130), (630, 1030)])
+def test_eed_step_under_each_tile_policy(shape):
+    """One EED step under every fixed tile policy (64 x 64 tiles exist for FOEED
+    only: EED takes 64 x 32 under h64): each matches the oracle inside a guard
+    band, and all give the same bits."""
+    rng = _rng(410)
+    h, w = shape
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    uprev = (ucur + 0.01 * rng.normal(size=shape)).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.08).astype(np.uint8)
+    ref = O.fsi_step(1, uprev, ucur, mask, 1.5, 0.25, 1.5, 0.03)
+    pitch = ((w + 3) // 4) * 4 + 4
+    outs = []
+    for policy in ("auto", "h16", "h32", "h64"):
+        (a, ab), (b, bb) = _guarded(uprev, pitch, torch.float32), _guarded(ucur, pitch, torch.float32)
+        m, mb = _guarded(mask, pitch, torch.uint8)
+        out, ob = _guarded(np.zeros(shape), pitch, torch.float32)
+        try:
+            fg.set_tile_policy(policy)
+            fg.eed_step(a, b, out, m, 1.5, 0.03, 1.5, tau=0.25)
+            torch.cuda.synchronize()
+        finally:
+            fg.set_tile_policy("auto")
+        assert all(_band_intact(x, w) for x in (ab, bb, mb, ob)), policy
+        outs.append(out.cpu().numpy())
+    np.testing.assert_allclose(outs[0].astype(np.float64), ref, rtol=0, atol=2e-5)
+    np.testing.assert_array_equal(outs[0][mask != 0], ucur[mask != 0])
+    for got in outs[1:]:
+        np.testing.assert_array_equal(got, outs[0])
+
+
 @pytest.mark.parametrize("g_kind,mu3", [(1, 0), (2, 1), (0, 2), (0, 1)])
 def test_generic_f32_variants(g_kind, mu3):
     rng = _rng(300 + g_kind)
