@@ -400,7 +400,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-convergence", action="store_true")
-    ap.add_argument("--tile-policy", default="auto", choices=["auto", "h32", "h16", "h64"],
+    ap.add_argument("--tile-policy", default="auto", choices=["auto", "h32", "h16", "h64", "h8"],
                     help="tile shape of the FP32 step kernel: timed once and kept (auto), or fixed; a fixed "
                          "shape keeps profiler runs, whose serialised launches distort the timing, on the "
                          "shape the benchmark uses")

@@ -267,8 +267,8 @@ foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask, void *u_in
  * FOEED_F32_F64U with the Charbonnier diffusivity and, for FOEED, mu3 =
  * sqrt(mu1); not in the paper, whose implementation is sequential). Each CTA
  * computes a 64 x 32 or a 64 x 16 block of output pixels, or, for a single
- * FOEED image, a 64 x 64 block. The shapes give bitwise the same results: only
- * the time differs.
+ * FOEED image, a 64 x 64 block (512 threads) or a 64 x 8 block (128 threads).
+ * The shapes give bitwise the same results: only the time differs.
  *   FOEED_TILES_AUTO (default): the solvers time the candidates and keep the
  *     fastest, once per (device, image size, method, Gaussian radius, precision)
  *     for a single image, and once per (device, list of image sizes, method,
@@ -277,9 +277,10 @@ foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask, void *u_in
  *     a tile count (a few thresholds from the batch's own sizes). The timing runs
  *     inside the first solve of its kind (a few step launches into workspace
  *     buffers that the solve overwrites) and is cached for the process; single
- *     FOEED images also try 64 x 64 tiles.
- *   FOEED_TILES_H64 / FOEED_TILES_H32 / FOEED_TILES_H16: that tile height for
- *     every image (64 only for single-image FOEED; elsewhere it means 32).
+ *     FOEED images also try 64 x 64 and 64 x 8 tiles.
+ *   FOEED_TILES_H64 / FOEED_TILES_H32 / FOEED_TILES_H16 / FOEED_TILES_H8: that
+ *     tile height for every image (64 and 8 only for single-image FOEED;
+ *     elsewhere 64 means 32 and 8 means 16).
  * The policy applies to the calling host thread's later calls: foeed_inpaint,
  * eed_inpaint and the batched solvers tune as above; foeed_step, eed_step,
  * foeed_inpaint_static and the forward steps of foeed_inpaint_vjp, which do
@@ -289,6 +290,7 @@ foeed_status foeed_inpaint_static(const void *f, const uint8_t *mask, void *u_in
  */
 typedef enum {
     FOEED_TILES_AUTO = 0,
+    FOEED_TILES_H8 = 8,  /* 64 x 8 tiles of 128 threads: single-image FOEED only (else 64 x 16) */
     FOEED_TILES_H16 = 16,
     FOEED_TILES_H32 = 32,
     FOEED_TILES_H64 = 64 /* 64 x 64 tiles of 512 threads: single-image FOEED only (else 64 x 32) */
@@ -299,7 +301,7 @@ foeed_status foeed_set_tile_policy(int policy);
  * calling thread. Times are microseconds per FSI step measured by the autotuner
  * (0 when it did not run for that solve, e.g. a cached or fixed choice). */
 typedef struct {
-    int tile_h;      /* single image: 64, 32 or 16 (0: the generic kernel ran); batch: 0 */
+    int tile_h;      /* single image: 64, 32, 16 or 8 (0: the generic kernel ran); batch: 0 */
     int images;      /* images in the solve */
     int images_h16;  /* images solved on 64 x 16 tiles */
     int tuned;       /* 1 if the autotuner timed the candidates for this solve */
@@ -307,6 +309,7 @@ typedef struct {
     float us_h16;    /* time of the plan with 64 x 16 tiles for every image */
     float us_chosen; /* time of the plan chosen */
     float us_h64;    /* single FOEED image: time with 64 x 64 tiles (0 otherwise) */
+    float us_h8;     /* single FOEED image: time with 64 x 8 tiles (0 otherwise) */
 } foeed_tile_plan;
 foeed_status foeed_last_tile_plan(foeed_tile_plan *out);
 

@@ -59,10 +59,11 @@ class _Report(C.Structure):
 
 class _TilePlan(C.Structure):
     _fields_ = [("tile_h", C.c_int), ("images", C.c_int), ("images_h16", C.c_int), ("tuned", C.c_int),
-                ("us_h32", C.c_float), ("us_h16", C.c_float), ("us_chosen", C.c_float), ("us_h64", C.c_float)]
+                ("us_h32", C.c_float), ("us_h16", C.c_float), ("us_chosen", C.c_float), ("us_h64", C.c_float),
+                ("us_h8", C.c_float)]
 
 
-TILE_POLICY = {"auto": 0, "h16": 16, "h32": 32, "h64": 64, 0: 0, 16: 16, 32: 32, 64: 64}
+TILE_POLICY = {"auto": 0, "h8": 8, "h16": 16, "h32": 32, "h64": 64, 0: 0, 8: 8, 16: 16, 32: 32, 64: 64}
 
 
 @dataclass

@@ -58,9 +58,13 @@ int tile_h(foeed_dtype d) { return d == FOEED_F64 ? kTileH64 : kTileH32; }
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocksMax = 1024;
 
+// Reduction partials one step or reduction can write: one per CTA of the
+// largest grid (FP32: the fast kernels' 64 x 8 tiles, the smallest they use).
+constexpr int kFastMinTileH = 8;
 long long max_blocks(int w, int h, foeed_dtype d)
 {
-    long long step = (long long)((w + tile_w(d) - 1) / tile_w(d)) * ((h + tile_h(d) - 1) / tile_h(d));
+    const int th = d == FOEED_F64 ? tile_h(d) : kFastMinTileH;
+    long long step = (long long)((w + tile_w(d) - 1) / tile_w(d)) * ((h + th - 1) / th);
     return step > kRedBlocksMax ? step : kRedBlocksMax;
 }
 
@@ -330,9 +334,15 @@ cudaError_t capture_stream(int dev, cudaStream_t *out)
 thread_local int g_tile_policy = FOEED_TILES_AUTO;
 thread_local foeed_tile_plan g_last_plan = {};
 
-// The tile height a fixed policy gives one image: 64 x 64 tiles exist for FOEED
-// only, so EED takes 64 x 32 under FOEED_TILES_H64.
-int fixed_tile_h(bool eed) { return (eed && g_tile_policy == FOEED_TILES_H64) ? FOEED_TILES_H32 : g_tile_policy; }
+// The tile height a fixed policy gives one image: 64 x 64 and 64 x 8 tiles exist
+// for FOEED only, so EED takes 64 x 32 under FOEED_TILES_H64 and 64 x 16 under
+// FOEED_TILES_H8.
+int fixed_tile_h(bool eed)
+{
+    if (eed && g_tile_policy == FOEED_TILES_H64) return FOEED_TILES_H32;
+    if (eed && g_tile_policy == FOEED_TILES_H8) return FOEED_TILES_H16;
+    return g_tile_policy;
+}
 
 struct TuneKey {
     int dev, eed, R, f64u, w, h, count, pad;
@@ -342,7 +352,7 @@ struct TuneKey {
 
 struct TuneVal {
     int choice;  // single image: tile height; batch: tile-count threshold of the 64 x 16 images
-    float us_h32, us_h16, us_h64, us_chosen;
+    float us_h32, us_h16, us_h64, us_h8, us_chosen;
 };
 
 std::mutex g_tune_mu;
@@ -420,15 +430,16 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
             CK(launch_step(eed, d, nullptr, p, s));
             cudaStream_t cs = nullptr;
             CK(capture_stream(dev, &cs));
-            // candidates: 64 x 32 and 64 x 16 tiles, and 64 x 64 for FOEED
-            const int th[3] = {32, 16, 64};
-            const int ncand = eed ? 2 : 3;
-            cudaGraphExec_t ex[3] = {nullptr, nullptr, nullptr};
+            // candidates: 64 x 32 and 64 x 16 tiles, and 64 x 64 and 64 x 8 for FOEED
+            constexpr int kCand = 4;
+            const int th[kCand] = {32, 16, 64, 8};
+            const int ncand = eed ? 2 : kCand;
+            cudaGraphExec_t ex[kCand] = {nullptr, nullptr, nullptr, nullptr};
             struct ExecGuard {
                 cudaGraphExec_t *e;
                 ~ExecGuard()
                 {
-                    for (int i = 0; i < 3; ++i)
+                    for (int i = 0; i < kCand; ++i)
                         if (e[i]) cudaGraphExecDestroy(e[i]);
                 }
             } guard{ex};
@@ -448,7 +459,7 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
                 if (err != cudaSuccess) return fail(FOEED_ERR_CUDA, "capturing the tile-shape timing: %s",
                                                     cudaGetErrorString(err));
             }
-            float us[3] = {-1.f, -1.f, -1.f};
+            float us[kCand] = {-1.f, -1.f, -1.f, -1.f};
             // the candidates alternate over kTuneRounds rounds and each keeps its
             // fastest time, so a clock still ramping up favours none
             for (int round = 0; round < kTuneRounds; ++round)
@@ -465,12 +476,14 @@ foeed_status choose_tile_h(bool eed, foeed_dtype d, const foeed_params &p, int w
             v.us_h32 = us[0];
             v.us_h16 = us[1];
             v.us_h64 = ncand > 2 ? us[2] : 0.f;
+            v.us_h8 = ncand > 3 ? us[3] : 0.f;
             v.us_chosen = us[best];
             tune_store(k, v);
             g_last_plan.tuned = 1;
             g_last_plan.us_h32 = v.us_h32;
             g_last_plan.us_h16 = v.us_h16;
             g_last_plan.us_h64 = v.us_h64;
+            g_last_plan.us_h8 = v.us_h8;
             g_last_plan.us_chosen = v.us_chosen;
             *tile_h = v.choice;
         }
@@ -774,8 +787,8 @@ foeed_status foeed_apply_tensor_field(const void *u, const void *d, void *Pu, in
 
 foeed_status foeed_set_tile_policy(int policy)
 {
-    if (policy != FOEED_TILES_AUTO && policy != FOEED_TILES_H16 && policy != FOEED_TILES_H32 &&
-        policy != FOEED_TILES_H64)
+    if (policy != FOEED_TILES_AUTO && policy != FOEED_TILES_H8 && policy != FOEED_TILES_H16 &&
+        policy != FOEED_TILES_H32 && policy != FOEED_TILES_H64)
         return fail(FOEED_ERR_ARG, "unknown tile policy %d", policy);
     g_tile_policy = policy;
     return FOEED_OK;
@@ -1196,7 +1209,8 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     };
     g_last_plan = foeed_tile_plan{};
     g_last_plan.images = count;
-    int thresh = g_tile_policy == FOEED_TILES_H16 ? INT_MAX : 0;  // a batch has no 64 x 64 tiles
+    // a batch has no 64 x 64 or 64 x 8 tiles: those policies mean 64 x 32 and 64 x 16 there
+    int thresh = (g_tile_policy == FOEED_TILES_H16 || g_tile_policy == FOEED_TILES_H8) ? INT_MAX : 0;
     if (g_tile_policy == FOEED_TILES_AUTO) {
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -1235,7 +1249,7 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
                     if (tc[ci] < 0.f || us < tc[ci]) tc[ci] = us;
                 }
             float best = -1.f;
-            v.us_h32 = v.us_h16 = v.us_h64 = 0.f;
+            v.us_h32 = v.us_h16 = v.us_h64 = v.us_h8 = 0.f;
             for (size_t ci = 0; ci < cand.size(); ++ci) {
                 if (cand[ci] == 0) v.us_h32 = tc[ci];
                 if (cand[ci] == INT_MAX) v.us_h16 = tc[ci];

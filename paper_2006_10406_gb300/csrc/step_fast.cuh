@@ -192,12 +192,13 @@ __device__ __forceinline__ void tensor_row(const float *sup, const float *sc, co
 }
 
 // Tile geometry: 64 x TH output pixels, TH = 32 (large images) or 16 (images
-// with fewer tiles than the GPU has SMs: more, shorter CTAs per step).
+// with fewer tiles than the GPU has SMs: more, shorter CTAs per step); for
+// single FOEED images also TH = 64 (512 threads) and TH = 8 (128 threads).
 template <int R, bool EED, int TH_ = 32>
 struct FastTile {
     static constexpr int TW = 64, TH = TH_;
-    static_assert(TH == 64 || TH == 32 || TH == 16, "tile height");
-    static constexpr int NTHR = TH == 64 ? 512 : 256;    // threads per CTA
+    static_assert(TH == 64 || TH == 32 || TH == 16 || TH == 8, "tile height");
+    static constexpr int NTHR = TH == 64 ? 512 : (TH == 8 ? 128 : 256);  // threads per CTA
     // CTAs per SM the register allocation is bounded for: the 54 KB of shared
     // memory of a 64 x 32 tile fit four 256-thread CTAs (64 registers each)
     static constexpr int MINB = 1024 / NTHR;
@@ -251,15 +252,16 @@ __device__ __forceinline__ void fast_tile(const StepArgs<float> &p, const TileIm
     const int w = im.w, h = im.h;
     const long pitch = im.pitch;
 
-    // ---- A: u window, copied global -> shared asynchronously (cp.async). Thread tid < 252
-    // owns the float4 column q = tid % 21 and the rows r0 = tid / 21, r0 + 12, ...; interior
-    // tiles copy 16 bytes per row with no index arithmetic beyond a pointer increment ----
+    // ---- A: u window, copied global -> shared asynchronously (cp.async). Thread tid < 21 RP
+    // owns the float4 column q = tid % 21 and the rows r0 = tid / 21, r0 + RP, ... (RP = 12
+    // with 256 threads); interior tiles copy 16 bytes per row with no index arithmetic
+    // beyond a pointer increment ----
     {
         const float *__restrict__ uc = im.ucur;
         const bool xin = (x0 - 8 >= 0) && (x0 + 76 <= w);
         const bool yin = (y0 - G::HL >= 0) && (y0 + G::TH + G::HL <= h);
         constexpr int NQ = G::SU_W / 4;                // 21 float4 per row
-        constexpr int RP = G::NTHR / NQ;                 // rows per pass (12, or 24 with 512 threads)
+        constexpr int RP = G::NTHR / NQ;                 // rows per pass (12; 24 / 6 with 512 / 128 threads)
         constexpr int NP = (G::SU_H + RP - 1) / RP;    // passes
         if (tid < RP * NQ) {
             const int q = tid % NQ, r0 = tid / NQ;
@@ -700,6 +702,9 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
             if (e != cudaSuccess) return e;
             e = cudaFuncSetAttribute(fsi_step_fast<R, EED, U, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)FastTile<R, EED, 64>::SMEM);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(fsi_step_fast<R, EED, U, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)FastTile<R, EED, 8>::SMEM);
         }
         return e;
     }
@@ -711,6 +716,13 @@ cudaError_t launch_fsi_step_fast(const StepArgs<float> *ap, cudaStream_t s)
             using G64 = FastTile<R, EED, 64>;
             dim3 grid(ntx, (ap->h + 63) / 64);
             return launch_step_kernel(fsi_step_fast<R, EED, U, 64>, grid, G64::NTHR, G64::SMEM, s, *ap);
+        }
+        // 64 x 8 tiles, 128 threads, up to eight CTAs per SM (FOEED only: a
+        // candidate of the autotuner for images under one wave of tiles)
+        if (ap->tile_h == 8) {
+            using G8 = FastTile<R, EED, 8>;
+            dim3 grid(ntx, (ap->h + 7) / 8);
+            return launch_step_kernel(fsi_step_fast<R, EED, U, 8>, grid, G8::NTHR, G8::SMEM, s, *ap);
         }
     }
     const bool h16 = ap->tile_h == 16 || (ap->tile_h != 32 && (long long)ntx * ((ap->h + 31) / 32) < kFastSmallTiles);

@@ -156,22 +156,22 @@ def test_messages_are_per_call():
 
 
 def test_tile_policy_arguments_are_checked_on_the_host():
-    """foeed_set_tile_policy accepts AUTO (0), 16, 32 and 64 only; foeed_last_tile_plan
+    """foeed_set_tile_policy accepts AUTO (0), 8, 16, 32 and 64 only; foeed_last_tile_plan
     rejects NULL. Neither touches the GPU."""
     import ctypes as C
 
     import paper_2006_10406_gb300 as fg
     L = fg.lib()
     try:
-        for bad in (1, 8, 128, -1):
+        for bad in (1, 4, 24, 128, -1):
             assert L.foeed_set_tile_policy(bad) == 1
             assert b"tile policy" in L.foeed_last_error()
-        for good in (16, 32, 64, 0):
+        for good in (8, 16, 32, 64, 0):
             assert L.foeed_set_tile_policy(good) == 0
         assert L.foeed_last_tile_plan(None) == 1
         plan = fg._TilePlan()
         assert L.foeed_last_tile_plan(C.byref(plan)) == 0
         with pytest.raises(KeyError):
-            fg.set_tile_policy("h8")
+            fg.set_tile_policy("h128")
     finally:
         L.foeed_set_tile_policy(0)

@@ -427,11 +427,12 @@ def test_fast_and_generic_f32_paths_match_oracle(method, shape, sigma):
         np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
 
 
-@pytest.mark.parametrize("policy", ["h16", "h32", "h64"])
+@pytest.mark.parametrize("policy", ["h8", "h16", "h32", "h64"])
 @pytest.mark.parametrize("shape", [(100, 130), (630, 1030), (70, 64), (130, 200)])
 def test_fast_step_each_tile_shape_matches_oracle(policy, shape):
-    """One FOEED step on each fixed tile shape (64 x 16, 64 x 32, 64 x 64 tiles with
-    512 threads), ragged in both directions, inside a guard band."""
+    """One FOEED step on each fixed tile shape (64 x 8 tiles with 128 threads,
+    64 x 16, 64 x 32, 64 x 64 tiles with 512 threads), ragged in both directions,
+    inside a guard band."""
     rng = _rng(400)
     h, w = shape
     ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
@@ -456,9 +457,9 @@ def test_fast_step_each_tile_shape_matches_oracle(policy, shape):
 
 @pytest.mark.parametrize("shape", [(100, 130), (630, 1030)])
 def test_eed_step_under_each_tile_policy(shape):
-    """One EED step under every fixed tile policy (64 x 64 tiles exist for FOEED
-    only: EED takes 64 x 32 under h64): each matches the oracle inside a guard
-    band, and all give the same bits."""
+    """One EED step under every fixed tile policy (64 x 64 and 64 x 8 tiles exist
+    for FOEED only: EED takes 64 x 32 under h64 and 64 x 16 under h8): each matches
+    the oracle inside a guard band, and all give the same bits."""
     rng = _rng(410)
     h, w = shape
     ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
@@ -467,7 +468,7 @@ def test_eed_step_under_each_tile_policy(shape):
     ref = O.fsi_step(1, uprev, ucur, mask, 1.5, 0.25, 1.5, 0.03)
     pitch = ((w + 3) // 4) * 4 + 4
     outs = []
-    for policy in ("auto", "h16", "h32", "h64"):
+    for policy in ("auto", "h8", "h16", "h32", "h64"):
         (a, ab), (b, bb) = _guarded(uprev, pitch, torch.float32), _guarded(ucur, pitch, torch.float32)
         m, mb = _guarded(mask, pitch, torch.uint8)
         out, ob = _guarded(np.zeros(shape), pitch, torch.float32)
@@ -526,18 +527,20 @@ def test_autotuned_solve_equals_each_fixed_tile_shape(method, shape):
         fg.set_tile_policy("auto")
         ua, _ = solve(f, m, lam, sigma, 8, 3)
         plan = fg.last_tile_plan()
-        assert plan["images"] == 1 and plan["tile_h"] in ((16, 32, 64) if method == 0 else (16, 32))
+        assert plan["images"] == 1 and plan["tile_h"] in ((8, 16, 32, 64) if method == 0 else (16, 32))
         if plan["tuned"]:
             times = {32: plan["us_h32"], 16: plan["us_h16"]}
-            if method == 0:
-                times[64] = plan["us_h64"]  # 64 x 64 tiles are a FOEED candidate only
+            if method == 0:  # 64 x 64 and 64 x 8 tiles are FOEED candidates only
+                times[64] = plan["us_h64"]
+                times[8] = plan["us_h8"]
             assert all(t > 0 for t in times.values())
             assert plan["us_chosen"] == min(times.values()) == times[plan["tile_h"]]
         ua2, _ = solve(f, m, lam, sigma, 8, 3)
         again = fg.last_tile_plan()
         assert again["tuned"] == 0 and again["tile_h"] == plan["tile_h"]  # the choice is cached
         assert torch.equal(ua, ua2)
-        for pol, th in (("h32", 32), ("h16", 16), ("h64", 64 if method == 0 else 32)):
+        for pol, th in (("h32", 32), ("h16", 16), ("h64", 64 if method == 0 else 32),
+                        ("h8", 8 if method == 0 else 16)):
             fg.set_tile_policy(pol)
             u, _ = solve(f, m, lam, sigma, 8, 3)
             assert fg.last_tile_plan()["tile_h"] == th
@@ -560,7 +563,7 @@ def test_autotuned_batch_equals_each_fixed_tile_plan(method):
         assert plan["images"] == len(imgs) and 0 <= plan["images_h16"] <= len(imgs)
         if plan["tuned"]:
             assert 0 < plan["us_chosen"] <= min(plan["us_h32"], plan["us_h16"])
-        for pol, nh16 in (("h32", 0), ("h16", len(imgs))):
+        for pol, nh16 in (("h32", 0), ("h16", len(imgs)), ("h8", len(imgs)), ("h64", 0)):
             fg.set_tile_policy(pol)
             u, _ = solve(imgs, masks, lams, 1.0, 6, 3)
             assert fg.last_tile_plan()["images_h16"] == nh16
