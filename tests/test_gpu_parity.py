@@ -455,6 +455,38 @@ def test_fast_step_each_tile_shape_matches_oracle(policy, shape):
     np.testing.assert_array_equal(got[mask != 0], ucur[mask != 0])
 
 
+@pytest.mark.parametrize("policy", ["h8", "h64"])
+@pytest.mark.parametrize("sigma", [0.0, 0.5, 1.0, 1.5, 2.0])
+def test_fast_step_small_and_large_tiles_every_radius(policy, sigma):
+    """The FOEED-only tile shapes (64 x 8 with 128 threads, 64 x 64 with 512) at
+    every Gaussian radius R = 0 .. 6, where the window's copy passes and the
+    x pass's taps change, ragged in both directions, inside a guard band; the
+    result equals the default shape's bitwise."""
+    rng = _rng(420)
+    shape = (75, 150)
+    h, w = shape
+    ucur = rng.uniform(size=shape).astype(np.float32).astype(np.float64)
+    uprev = (ucur + 0.01 * rng.normal(size=shape)).astype(np.float32).astype(np.float64)
+    mask = (rng.uniform(size=shape) < 0.08).astype(np.uint8)
+    ref = O.fsi_step(0, uprev, ucur, mask, 1.5, 0.05, sigma, 0.03)
+    pitch = ((w + 3) // 4) * 4 + 4
+    outs = []
+    for pol in ("auto", policy):
+        (a, ab), (b, bb) = _guarded(uprev, pitch, torch.float32), _guarded(ucur, pitch, torch.float32)
+        m, mb = _guarded(mask, pitch, torch.uint8)
+        out, ob = _guarded(np.zeros(shape), pitch, torch.float32)
+        try:
+            fg.set_tile_policy(pol)
+            fg.foeed_step(a, b, out, m, 1.5, 0.03, sigma, tau=0.05)
+            torch.cuda.synchronize()
+        finally:
+            fg.set_tile_policy("auto")
+        assert all(_band_intact(x, w) for x in (ab, bb, mb, ob)), pol
+        outs.append(out.cpu().numpy())
+    np.testing.assert_allclose(outs[1].astype(np.float64), ref, rtol=0, atol=2e-5)
+    np.testing.assert_array_equal(outs[1], outs[0])
+
+
 @pytest.mark.parametrize("shape", [(100, 130), (630, 1030)])
 def test_eed_step_under_each_tile_policy(shape):
     """One EED step under every fixed tile policy (64 x 64 and 64 x 8 tiles exist
