@@ -313,6 +313,30 @@ def gradient_once(fg, synth, torch, dev, rank, checkpoint_every=16):
                           "grad_norm": float(gf.norm())}), flush=True)
 
 
+def batch_once(fg, synth, torch, dev, rank, tile_policy="auto"):
+    """One warm-up (one FSI cycle) and one timed solve (two cycles of 25 steps) of
+    the W4 batch of 256 images, for profiler launch lists of the batched step."""
+    import numpy as np
+    cases = synth.batched_workload(256)
+    imgs = [torch.from_numpy(c[0].astype(np.float32)).to(dev) for c in cases]
+    masks = [torch.from_numpy(c[1]).to(dev) for c in cases]
+    lams = [float(c[2]) for c in cases]
+    fg.set_tile_policy(tile_policy)
+    fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 25, 1)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fg.foeed_inpaint_batch(imgs, masks, lams, 1.0, 25, 2)
+    b.record()
+    torch.cuda.synchronize(dev)
+    if rank == 0:
+        pixels = sum(int(im.numel()) for im in imgs)
+        ms = a.elapsed_time(b)
+        print(json.dumps({"batch_ms": ms, "images": len(imgs), "pixels": pixels, "steps": 50,
+                          "pixel_updates_per_s": pixels * 50 / (ms / 1e3), "tile_plan": fg.last_tile_plan()}),
+              flush=True)
+
+
 def adjoint_leg(fg, synth, torch, dev, stream):
     """W5 tonal optimisation: 1024 x 1024 FP32, 4% mask, 30 FSI cycles of length 20
     unrolled; 20 Adam steps on the stored grey values with the gradient of the
@@ -411,6 +435,9 @@ def main():
     ap.add_argument("--gradient-only", action="store_true",
                     help="only one warm-up and one timed gradient of the 1024^2 tonal-optimisation "
                          "workload (for profiler launch lists of the backward kernels)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only one warm-up and one timed two-cycle solve of the 256-image batch "
+                         "(for profiler launch lists of the batched step kernel)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -427,6 +454,8 @@ def main():
     dev = torch.device("cuda", local)
     if args.gradient_only:
         return gradient_once(fg, synth, torch, dev, rank, args.checkpoint_every)
+    if args.batched_only:
+        return batch_once(fg, synth, torch, dev, rank, args.tile_policy)
     pg = None
     if world > 1:
         import torch.distributed as dist
