@@ -39,8 +39,8 @@ WORKLOAD = 3
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel on the full 2048x2048 workload, and the hash of the
 # kernel source it was taken on; reported only while the source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "122bb39f0af958b73f6ab23544f00b092d67380b",
-               "bytes_per_launch": 37793280 + 10240}  # from the ncu capture summary of this kernel
+NCU_TRAFFIC = {"source_sha1": "ae657531a038fd4f6fb6f8bd2597053c49cd13c1",
+               "bytes_per_launch": 37793536 + 32000}  # from the ncu capture summary of this kernel
 
 
 def kernel_source_sha1():

@@ -1,10 +1,13 @@
 // Register-blocked FP32 fused FSI step (FOEED with Charbonnier g and
 // mu3 = sqrt(mu1), or EED with Charbonnier g): the hot kernel of the solver.
 //
-// One CTA of 256 threads owns a 64 x 32 output tile. Every stage works on
-// groups of four consecutive pixels of one row (float4 in shared memory), and
-// each thread keeps a small block of rows or columns in registers so that a
-// shared-memory value is loaded once for several outputs:
+// One CTA of 256 threads owns a 64 x 32 output tile (64 x 16 for small images;
+// for single FOEED images the autotuner also tries 64 x 64 tiles of 512 threads
+// and 64 x 8 tiles of 128). Every stage works on groups of four consecutive
+// pixels of one row (float4 in shared memory), and each thread keeps a small
+// block of rows or columns in registers so that a shared-memory value is
+// loaded once for several outputs (the row ranges below are those of a 64 x 32
+// tile):
 //   A  u^k window, rows tile-(R+2) .. tile+31+(R+2), columns tile-8 .. tile+75
 //      (cp.async 16-byte copies for interior columns, mirrored 4-byte copies at
 //      the image border)
