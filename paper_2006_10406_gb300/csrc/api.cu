@@ -230,6 +230,57 @@ struct EventPair {
     }
 };
 
+// Independent per-image launches of a batch (set-up, copy-out) spread over a
+// few side streams forked from the caller's stream and joined back to it. The
+// streams are created once per device and kept for the process.
+constexpr int kSideStreams = 4;
+cudaError_t side_streams(cudaStream_t *out)
+{
+    static std::mutex mu;
+    static std::map<int, std::vector<cudaStream_t>> pool;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<cudaStream_t> &v = pool[dev];
+    while ((int)v.size() < kSideStreams) {
+        cudaStream_t st = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        v.push_back(st);
+    }
+    for (int k = 0; k < kSideStreams; ++k) out[k] = v[k];
+    return cudaSuccess;
+}
+
+struct Fork {
+    cudaStream_t st[kSideStreams] = {};
+    cudaEvent_t ev[kSideStreams + 1] = {};
+    // the side streams wait for everything queued on s so far
+    cudaError_t open(cudaStream_t s)
+    {
+        cudaError_t e = side_streams(st);
+        for (int k = 0; k <= kSideStreams && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[kSideStreams], s);
+        for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st[k], ev[kSideStreams], 0);
+        return e;
+    }
+    cudaStream_t operator[](int i) const { return st[i % kSideStreams]; }
+    // s waits for everything queued on the side streams
+    cudaError_t join(cudaStream_t s)
+    {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) e = cudaEventRecord(ev[k], st[k]);
+        for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s, ev[k], 0);
+        return e;
+    }
+    ~Fork()
+    {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
 struct StepCall {
     const void *uprev, *ucur, *c0;
     void *unext;
@@ -1175,11 +1226,16 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
     CK(evs.create());
     cudaEvent_t ev0 = evs.e[0], ev1 = evs.e[1];
     CK(cudaEventRecord(ev0, s));
-    for (int i = 0; i < count; ++i) {
-        const Layout &L = bp.lay[i];
-        CK(cudaMemcpyAsync(ws + bp.off[i] + L.ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        CK(launch_prep<float>(inst[i].f, inst[i].mask, inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch,
-                              bp.lay[i], ws + bp.off[i], p.init_mode, s));
+    {
+        Fork fk;
+        CK(fk.open(s));
+        for (int i = 0; i < count; ++i) {
+            const Layout &L = bp.lay[i];
+            CK(cudaMemcpyAsync(ws + bp.off[i] + L.ctl, &h0, sizeof(Ctl), cudaMemcpyHostToDevice, fk[i]));
+            CK(launch_prep<float>(inst[i].f, inst[i].mask, inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch,
+                                  bp.lay[i], ws + bp.off[i], p.init_mode, fk[i]));
+        }
+        CK(fk.join(s));
     }
 
     // tile plan: the thread's fixed policy, the cached choice for this list of
@@ -1315,8 +1371,14 @@ static foeed_status inpaint_batch(bool eed, const foeed_instance *inst, int coun
             if (all) break;
         }
     }
-    for (int i = 0; i < count && err == cudaSuccess; ++i)
-        err = launch_copy_out<float>(bp.lay[i], ws + bp.off[i], inst[i].u_inout, inst[i].w, inst[i].h, inst[i].pitch, s);
+    if (err == cudaSuccess) {
+        Fork fk;
+        err = fk.open(s);
+        for (int i = 0; i < count && err == cudaSuccess; ++i)
+            err = launch_copy_out<float>(bp.lay[i], ws + bp.off[i], inst[i].u_inout, inst[i].w, inst[i].h,
+                                         inst[i].pitch, fk[i]);
+        if (err == cudaSuccess) err = fk.join(s);
+    }
     if (err == cudaSuccess) err = cudaEventRecord(ev1, s);
     for (int i = 0; i < count && err == cudaSuccess; ++i)
         err = cudaMemcpyAsync(&hc[i], hi[i].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
